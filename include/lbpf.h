@@ -1,0 +1,177 @@
+/*
+ * lbpf.h -- C ABI of the GB300 (sm_103a) lattice-Boltzmann phase-field solver.
+ *
+ * The solver advances the coupled phase field phi, supersaturation U and
+ * temperature theta of Cartalade, Younsi & Plapp (arXiv 1602.07483, Sec. 2,
+ * Eqs. PhaseField_KarmaRappel, Concentration_Echebarria, Temp_Ramirez) with
+ * the lattice-Boltzmann schemes of Sec. 3:
+ *   - phi: non-local BGK collision, Eqs. (LBE_Eq_Phase)-(LBE_RelaxationTime)
+ *     and the collision stage of Sec. 3.4, anisotropy Eq. (Anisotropic-
+ *     Function_As) or Eq. (As_K41-K61), N vector Eq. (TermesAnisotropes);
+ *   - U: BGK with the modified equilibrium, Eqs. (Supersaturation_Bis)-
+ *     (RelaxationTime_Concentration), anti-trapping Eq. (AntiTrapping_Current);
+ *   - theta: standard BGK with a source, Eqs. (LBE_Eq_Temp)-(ThermalDiffusivity);
+ *   - streaming with bounce-back zero-flux walls (Sec. 3.4, Sec. 4).
+ * Lattices D3Q7, D3Q15, D3Q19 (Tables 1-2).  One step is: phi collision and
+ * streaming with phi^n, U^n, theta^n; then U and theta with phi^{n+1} and
+ * dphi/dt = (phi^{n+1} - phi^n)/dt (Sec. 3.4, "Algorithm implementation").
+ *
+ * Conventions for every call:
+ *   - Return value: LBPF_OK (0) or a negative LBPF_E* code; lbpf_strerror()
+ *     names it.  A CUDA failure is sticky: every later call on the handle
+ *     returns LBPF_ECUDA.
+ *   - Host arrays are owned by the caller, FP64, site-major with x fastest:
+ *     index ((z*ny + y)*nx + x).  Population arrays are population-major,
+ *     [Q][nz][ny][nx], in the paper's direction order (Table 1), and hold the
+ *     POST-STREAMING populations g_i(x,t), h_i(x,t), f_i(x,t).
+ *   - Device memory is owned by the handle (allocated in lbpf_create, freed
+ *     in lbpf_destroy).  Work is enqueued on the caller's CUDA stream (or the
+ *     legacy default stream when NULL); calls that return host data
+ *     synchronise that stream.
+ *   - There is no CPU fallback: without a usable CUDA device lbpf_create
+ *     returns LBPF_ECUDA.
+ *   - Handles are not thread-safe; use one handle per host thread.
+ */
+#ifndef LBPF_H
+#define LBPF_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBPF_OK 0
+#define LBPF_EINVAL (-1)    /* bad argument (sizes, lattice, null pointer) */
+#define LBPF_EUNSTABLE (-2) /* parameters give a relaxation time <= 1/2 somewhere */
+#define LBPF_ENOMEM (-3)    /* device allocation failed */
+#define LBPF_ENAN (-4)      /* a non-finite value was found in the fields */
+#define LBPF_ETIMEOUT (-5)  /* a bounded device wait gave up */
+#define LBPF_ECUDA (-6)     /* CUDA runtime error (sticky) */
+
+/* storage of the distributions; arithmetic is FP64 for LBPF_F64, FP32 otherwise */
+#define LBPF_F64 0
+#define LBPF_F32 1
+#define LBPF_F16 2  /* (f - shift) * scale in binary16, decoded to FP32 */
+#define LBPF_BF16 3 /* same codec in bfloat16 */
+
+/* field mask for lbpf_read_fields */
+#define LBPF_PHI 1u
+#define LBPF_U 2u
+#define LBPF_THETA 4u
+
+typedef struct {
+  int32_t nx, ny, nz; /* nodes per edge, each >= 1 */
+} lbpf_grid;
+
+typedef struct {
+  int32_t q_phi;   /* 7 | 15 | 19 */
+  int32_t q_u;     /* 7 | 15 | 19 */
+  int32_t q_theta; /* 0 (theta frozen at theta0) | 7 | 15 | 19 */
+} lbpf_lattice;
+
+typedef struct {
+  double W0, tau0;      /* interface width, relaxation time (Eq. PhaseField_KarmaRappel) */
+  double D, kappa;      /* solute and thermal diffusivity */
+  double lambda;        /* coupling constant */
+  double Mc_inf;        /* scaled liquidus slope M c_inf */
+  double k;             /* partition coefficient, 0 < k <= 1 */
+  int32_t aniso;        /* 0: Eq. (Anisotropic-Function_As); 1: Eq. (As_K41-K61) */
+  double eps1, eps2;    /* aniso 0: eps_s, unused; aniso 1: eps_s, delta */
+  double dx, dt;        /* lattice spacing and time step */
+  int32_t antitrapping; /* 1: anti-trapping current on; 0: off */
+  int32_t storage;      /* LBPF_F64 | LBPF_F32 | LBPF_F16 | LBPF_BF16 */
+  double grad2_min;     /* |grad phi|^2 below which n, N, j_at are taken as 0 and a_s = 1;
+                           0 selects the default 1e-12 */
+} lbpf_params;
+
+typedef struct lbpf_sim lbpf_sim;
+
+/* Create a simulation on the current CUDA device.  Validates every argument,
+ * derives the relaxation times eta_U (Eq. RelaxationTime_Concentration) and
+ * eta_theta (Eq. ThermalDiffusivity), and rejects parameter sets for which
+ * a_s^2 eta_phi(a_s) <= 1/2 for some orientation (the non-local collision then
+ * over-relaxes), or eta_U, eta_theta <= 1/2, with LBPF_EUNSTABLE.  Allocates all
+ * device state (two copies of each distribution, three levels of phi, two of
+ * U and theta).  `cuda_stream` is a cudaStream_t or NULL; it is borrowed.
+ * The state is zero until lbpf_init_seed or lbpf_set_state. */
+int lbpf_create(const lbpf_grid* grid, const lbpf_lattice* lattice, const lbpf_params* params,
+                void* cuda_stream, lbpf_sim** out);
+
+/* Initial condition of Sec. 4: n_seeds diffuse spheres
+ * phi = tanh((R - r) dx / (sqrt2 W0)) (the largest value where seeds overlap),
+ * U = U0 and theta = theta0 everywhere.  centres: 3*n_seeds lattice coordinates
+ * (x,y,z; fractional allowed), radii: n_seeds lattice units.  Populations start
+ * at g = w phi, h = (A + B q/zeta) U, f = w theta.  Resets the step counter. */
+int lbpf_init_seed(lbpf_sim* sim, int32_t n_seeds, const double* centres, const double* radii,
+                   double U0, double theta0);
+
+/* Replace the state by post-streaming populations from the host (FP64, layout
+ * above; f may be NULL when q_theta == 0).  Moments are recomputed as sums of
+ * the populations; theta0 is the frozen temperature when q_theta == 0.
+ * Resets the step counter.  Synchronous. */
+int lbpf_set_state(lbpf_sim* sim, const double* g, const double* h, const double* f, double theta0);
+
+/* Copy the post-streaming populations to the host (FP64; any pointer may be
+ * NULL to skip that field).  Synchronous. */
+int lbpf_get_state(lbpf_sim* sim, double* g, double* h, double* f);
+
+/* Enqueue n_steps time steps (asynchronous).  Steps are replayed from a CUDA
+ * graph captured on first use.  Returns LBPF_OK, or a sticky error. */
+int lbpf_step(lbpf_sim* sim, int64_t n_steps);
+
+/* Copy phi, U and/or theta (as selected by mask) of the current step to the
+ * host in FP64; unselected pointers may be NULL.  Synchronous. */
+int lbpf_read_fields(lbpf_sim* sim, uint32_t mask, double* phi, double* U, double* theta);
+
+/* FP64 sums over all sites, computed on the device in a fixed order:
+ * out[0] = sum phi, out[1] = sum U, out[2] = sum theta,
+ * out[3] = sum zeta(phi) (1 + (1-k) U)  (total solute, c / c_inf).
+ * Returns LBPF_ENAN (after filling out) when any sum is not finite.  Synchronous. */
+int lbpf_sums(lbpf_sim* sim, double out[4]);
+
+/* Dendrite tip along +x from node `centre` (3 ints): the first crossing
+ * phi_i >= 0 > phi_{i+1}, linearly interpolated, in lattice units (-1 when none).
+ * rho (may be NULL): tip radius in lattice units from a least-squares parabola
+ * x(j) = x_tip - j^2 / (2 rho) through the crossings of rows j = +-1..+-4 in the
+ * xy and xz planes through the centre, averaged (-1 when undefined).  Synchronous. */
+int lbpf_tip(lbpf_sim* sim, const int32_t centre[3], double* x_tip, double* rho);
+
+/* Number of steps taken since the last init / set_state / load. */
+int64_t lbpf_steps_done(const lbpf_sim* sim);
+
+/* Checkpoint: write / read a self-describing binary file (header with grid,
+ * lattices, parameters, step count, then the post-streaming populations in
+ * FP64).  lbpf_load requires a handle created with the same grid and lattices. */
+int lbpf_save(lbpf_sim* sim, const char* path);
+int lbpf_load(lbpf_sim* sim, const char* path);
+
+/* Tiling of the step kernels: block rows `by` (4..32, block is 32 x by
+ * threads) and z-chunk length (>= 1; the z range is split into chunks that are
+ * processed by separate thread blocks).  0 keeps the current value.  Takes
+ * effect at the next lbpf_step (the step graph is re-captured). */
+int lbpf_set_tiling(lbpf_sim* sim, int32_t by, int32_t zchunk);
+int lbpf_get_tiling(const lbpf_sim* sim, int32_t* by, int32_t* zchunk);
+
+/* Autotuner: times `steps` steps for each candidate tiling on a snapshot of
+ * the current state, keeps the fastest, and restores the state.  best_ms
+ * (may be NULL) receives the best time per step.  Synchronous. */
+int lbpf_autotune(lbpf_sim* sim, int32_t steps, double* best_ms);
+
+int lbpf_destroy(lbpf_sim* sim);
+
+/* Batched stepping: `n` handles created with identical lattices and storage
+ * (grids and physical parameters may differ) advance together, one launch per
+ * kernel phase covering the tiles of all simulations, captured in one CUDA
+ * graph.  The batch borrows the handles; destroy the batch before them. */
+typedef struct lbpf_batch lbpf_batch;
+int lbpf_batch_create(int32_t n, lbpf_sim* const* sims, void* cuda_stream, lbpf_batch** out);
+int lbpf_batch_step(lbpf_batch* batch, int64_t n_steps);
+int lbpf_batch_destroy(lbpf_batch* batch);
+
+/* Static description of an error code. */
+const char* lbpf_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBPF_H */
