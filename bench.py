@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Benchmark: coupled phi/U/theta lattice-Boltzmann site-updates per second.
+
+Workload: 512^3 nodes, D3Q19 for phi, U and theta, FP32 storage and arithmetic,
+two-harmonic anisotropy (eps = -0.02, delta = 0.015), four seeds R0 = 6 placed by
+default_rng(7) at least 80 cells apart, Delta = 0.5, theta0 = -0.3 (seeded,
+synthetic; shaped like the paper's 3D dendrite runs).  One step = the phase-field
+kernel plus the U/theta kernel (all populations read once and written once).
+
+Own arm (default): N ranks each advance an independent replica (weak scaling).
+`value` = sites x steps x ranks / max-over-ranks device time.  The JSON line also
+carries the roofline of the dominant kernel (k_uth, 38 populations per site), the
+FP64 oracle's throughput on a bounded sample (cpu_baseline), an end-to-end number
+through the C ABI with host buffers, and the SM clocks seen during the timed region.
+
+Reference arm (--impl reference): the FP64 CPU oracle on the host cores, on a
+bounded sample of the same workload (there is no GPU reference implementation).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled phi/U/theta site-updates/s (GLUPS) and % HBM roofline, FP32/FP16 vs FP64"
+UNIT = "GLUPS"
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_rate(budget_s=12.0, edge=64, threads=None):
+    """FP64 oracle site-updates/s on a bounded sample of the workload: a edge^3 box with
+    the same lattices and parameters and one seed, stepped until the time budget is used."""
+    import oracle
+    from paper_1602_07483_gb300 import workloads
+    w = workloads.large_kh(512)
+    p = dict(w.params)
+    s = oracle.Sim((edge, edge, edge), w.lattices, params=oracle.make_params(**p))
+    s.init_seed([[edge / 2, edge / 2, edge / 2]], [6.0], w.U0, w.theta0)
+    s.step(1)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        s.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or steps >= 400:
+            break
+    rate = edge ** 3 * steps / el
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return rate / 1e9, {"value": rate / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+                        "sample": "%d^3 box of the 512^3 D3Q19x3 workload (same parameters, one seed), "
+                                  "%d steps in %.1f s, FP64, OpenMP over z" % (edge, steps, el)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    vals = []
+    t_all = time.perf_counter()
+    for _ in range(args.warmup):
+        oracle_rate(budget_s=2.0, edge=48)
+    for _ in range(args.steps):
+        v, _ = oracle_rate(budget_s=max(2.0, min(12.0, 60.0 / max(1, args.steps))), edge=64)
+        vals.append(v)
+    value = statistics.median(vals)
+    _, cb = oracle_rate(budget_s=1.0, edge=32)
+    cb["value"] = value
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "kh512_q19x3 (bounded CPU sample: 64^3 box per step)",
+                   "grid": [512, 512, 512], "lattices": [19, 19, 19]},
+        "cpu_baseline": cb,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": time.perf_counter() - t_all,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_own(args):
+    import numpy as np
+    import torch
+    from paper_1602_07483_gb300 import build, lbpf, workloads
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    build.build()
+    st = torch.cuda.Stream()  # a real stream: the library enqueues on it and events are recorded on it
+    torch.cuda.set_stream(st)
+    w = workloads.large_kh(args.n)
+    hbm, peak_src = measured_peaks()
+
+    def barrier_sync():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    sim = lbpf.Sim(w.grid, w.lattices, storage="f32", stream=st.cuda_stream, **w.params)
+    sim.init_seed(w.centres, w.radii, w.U0, w.theta0)
+    if args.autotune:
+        sim.autotune(steps=2)
+    by, zchunk = sim.get_tiling()
+    sim.step(args.warmup)
+    barrier_sync()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    ms_phi, ms_uth, ms_span = sim.step_timed(args.steps)
+    barrier_sync()
+    clk = clocks.stop()
+    t_local = ms_span / 1e3
+    t = torch.tensor([t_local], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    t_max = float(t.item())
+    sites = w.sites
+    value = sites * args.steps * world / t_max / 1e9
+    # roofline of the dominant kernel: algorithmic bytes = read + write of every population it owns
+    q_phi, q_u, q_t = w.lattices
+    s_bytes = 4
+    bytes_uth = 2 * s_bytes * (q_u + q_t) * sites
+    bytes_phi = 2 * s_bytes * q_phi * sites
+    uth_ms = ms_uth / args.steps
+    phi_ms = ms_phi / args.steps
+    dom = ("k_uth", bytes_uth, uth_ms) if ms_uth >= ms_phi else ("k_phi", bytes_phi, phi_ms)
+    achieved = dom[1] / (dom[2] * 1e-3) / 1e9
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            with open(tr_path) as f:
+                tr = json.load(f)
+            ent = tr.get(dom[0])
+            if ent and ent.get("source_hash") == kernel_source_hash():
+                traffic = ent["bytes_per_launch_full"]
+        except Exception:
+            traffic = None
+    step_alg = 2 * s_bytes * (q_phi + q_u + q_t) * sites / (t_max / args.steps) / 1e9
+
+    # end to end through the C ABI: seeds uploaded from host memory, each step followed by a
+    # device->host read of the step's diagnostics (FP64 sums), final phi field read back to pinned memory
+    e2e = None
+    if rank == 0 or world > 1:
+        ke = max(2, args.steps // 2)
+        phi_host = torch.empty((args.n, args.n, args.n), dtype=torch.float64, pin_memory=True).numpy()
+        barrier_sync()
+        t0 = time.perf_counter()
+        sim.init_seed(w.centres, w.radii, w.U0, w.theta0)
+        for _ in range(ke):
+            sim.step(1)
+            sim.sums(check=False)
+        sim.read_fields(lbpf.LBPF_PHI, out=[phi_host, None, None])
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        tt = torch.tensor([te], dtype=torch.float64, device="cuda")
+        if world > 1:
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        te = float(tt.item())
+        h2d = (w.centres.size + w.radii.size) * 8 / ke
+        d2h = 32 + sites * 8 / ke
+        e2e = {"value": sites * ke * world / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": ke,
+               "what": "lbpf_init_seed from host seeds, then per step lbpf_step(1) + lbpf_sums (D2H), "
+                       "then lbpf_read_fields(phi) into pinned host memory"}
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+
+    variants = {}
+    if args.variants and rank == 0 and world == 1:
+        variants = run_variants(args, st)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        try:
+            _, cpu = oracle_rate(budget_s=12.0, edge=64)
+        except Exception as e:  # the CPU leg must not hide the GPU result
+            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": "failed: %s" % e}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "kh512_q19x3_f32", "grid": [args.n] * 3, "lattices": [q_phi, q_u, q_t],
+                       "storage": "f32", "anisotropy": "K41+K61 eps=-0.02 delta=0.015", "seeds": 4,
+                       "l2": "inputs larger than L2 (%.1f GB of populations)" % (2 * s_bytes * 57 * sites / 1e9),
+                       "tiling": {"block": [32, by], "zchunk": zchunk}, "parallelism": "replicas x%d" % world},
+            "roofline": {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
+                         "alg_bytes_per_launch": dom[1], "ms_per_launch": dom[2],
+                         "phi_kernel": {"ms": phi_ms, "GBps": bytes_phi / (phi_ms * 1e-3) / 1e9},
+                         "uth_kernel": {"ms": uth_ms, "GBps": bytes_uth / (uth_ms * 1e-3) / 1e9},
+                         "step_alg_GBps": step_alg, "step_frac": step_alg / hbm},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk,
+            "variants": variants,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("lbpf_dev.cuh",):
+        with open(os.path.join(ROOT, "paper_1602_07483_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def run_variants(args, st):
+    """FP16-storage form at 512^3 and the plain FP64 form at 256^3 (same workload recipe)."""
+    import torch
+    from paper_1602_07483_gb300 import lbpf, workloads
+    out = {}
+    for storage, n, k in (("f16", args.n, 10), ("f64", 256, 6)):
+        w = workloads.large_kh(n)
+        s = lbpf.Sim(w.grid, w.lattices, storage=storage, stream=st.cuda_stream, **w.params)
+        s.init_seed(w.centres, w.radii, w.U0, w.theta0)
+        s.step(3)
+        torch.cuda.synchronize()
+        ms_phi, ms_uth, span = s.step_timed(k)
+        sb = {"f16": 2, "f64": 8}[storage]
+        glups = w.sites * k / (span * 1e-3) / 1e9
+        out[storage] = {"grid": n, "GLUPS": glups, "ms_per_step": span / k,
+                        "alg_GBps": glups * 2 * sb * 57, "bound": "hbm" if storage != "f64" else "alu (FP64 rate)"}
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--n", type=int, default=512, help="grid edge (the workload is defined at 512)")
+    ap.add_argument("--autotune", type=int, default=0)
+    ap.add_argument("--variants", type=int, default=1)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_own(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -25,9 +25,9 @@
  *     [Q][nz][ny][nx], in the paper's direction order (Table 1), and hold the
  *     POST-STREAMING populations g_i(x,t), h_i(x,t), f_i(x,t).
  *   - Device memory is owned by the handle (allocated in lbpf_create, freed
- *     in lbpf_destroy).  Work is enqueued on the caller's CUDA stream (or the
- *     legacy default stream when NULL); calls that return host data
- *     synchronise that stream.
+ *     in lbpf_destroy).  Work is enqueued on the caller's CUDA stream (or on
+ *     a non-blocking stream owned by the handle when NULL); calls that return
+ *     host data synchronise that stream.
  *   - There is no CPU fallback: without a usable CUDA device lbpf_create
  *     returns LBPF_ECUDA.
  *   - Handles are not thread-safe; use one handle per host thread.
@@ -118,6 +118,13 @@ int lbpf_get_state(lbpf_sim* sim, double* g, double* h, double* f);
 /* Enqueue n_steps time steps (asynchronous).  Steps are replayed from a CUDA
  * graph captured on first use.  Returns LBPF_OK, or a sticky error. */
 int lbpf_step(lbpf_sim* sim, int64_t n_steps);
+
+/* Same as lbpf_step but without graphs: each kernel launch is bracketed by CUDA
+ * events recorded on the handle's stream, and the call returns (synchronously)
+ * the summed device time of the phase-field kernels in ms_kernels[0], of the
+ * U/theta kernels in ms_kernels[1], and the wall span of the n steps in
+ * ms_kernels[2].  Used to measure per-kernel bandwidth. */
+int lbpf_step_timed(lbpf_sim* sim, int64_t n_steps, double ms_kernels[3]);
 
 /* Copy phi, U and/or theta (as selected by mask) of the current step to the
  * host in FP64; unselected pointers may be NULL.  Synchronous. */

@@ -1,0 +1,924 @@
+// lbpf_api.cu -- host runtime behind the C ABI of include/lbpf.h.
+//
+// Owns the device state of a simulation, validates parameters, builds the
+// tile work lists of the step kernels, captures the time loop in CUDA graphs
+// (six steps per graph: populations alternate with period 2 and the phi levels
+// with period 3), and moves state between the host convention
+// (post-streaming populations, FP64) and the device pull layout.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "../../include/lbpf.h"
+#include "lbpf_aux.cuh"
+#include "lbpf_table.h"
+
+using namespace lbpf;
+
+namespace {
+
+constexpr int kGraphSteps = 6;
+
+int q_index(int q) { return q == 7 ? 0 : (q == 15 ? 1 : (q == 19 ? 2 : -1)); }
+int qt_index(int q) { return q == 0 ? 0 : (q == 7 ? 1 : (q == 15 ? 2 : (q == 19 ? 3 : -1))); }
+double lattice_e2(int q) { return q == 7 ? 0.25 : 1.0 / 3.0; }
+
+const KernelTable* table_for(int storage) {
+  switch (storage) {
+    case LBPF_F64: return &table_f64();
+    case LBPF_F32: return &table_f32();
+    case LBPF_F16: return &table_f16();
+    case LBPF_BF16: return &table_bf16();
+    default: return nullptr;
+  }
+}
+
+// a_s(n) of the two anisotropy functions (Eq. Anisotropic-Function_As, Eq. As_K41-K61)
+double aniso_host(int kind, double e1, double e2, double nx, double ny, double nz) {
+  const double r = sqrt(nx * nx + ny * ny + nz * nz);
+  nx /= r; ny /= r; nz /= r;
+  const double s4 = nx * nx * nx * nx + ny * ny * ny * ny + nz * nz * nz * nz;
+  if (kind == 0) return 1.0 - 3.0 * e1 + 4.0 * e1 * s4;
+  const double p3 = nx * nx * ny * ny * nz * nz;
+  return 1.0 + e1 * (s4 - 0.6) + e2 * (3.0 * s4 + 66.0 * p3 - 17.0 / 7.0);
+}
+
+// Smallest a_s^2 eta_phi(a_s) over interface orientations.  The non-local
+// collision relaxes a uniform perturbation at the rate 1/(a_s^2 eta_phi), which
+// must stay below 2.  Sampled on a fine grid of the unit sphere (a_s is smooth).
+double min_effective_tau(int kind, double e1, double e2, double c_eta, double* amin_out) {
+  double best = 1e300, amin = 1e300;
+  const int NT = 181, NP = 360;
+  for (int it = 0; it < NT; ++it) {
+    const double th = M_PI * it / (NT - 1);
+    for (int ip = 0; ip < NP; ++ip) {
+      const double ph = 2.0 * M_PI * ip / NP;
+      const double a = aniso_host(kind, e1, e2, sin(th) * cos(ph), sin(th) * sin(ph), cos(th) + 1e-300);
+      const double a2 = a * a;
+      best = std::min(best, a2 * (c_eta * a2 + 0.5));
+      amin = std::min(amin, a);
+    }
+  }
+  // the cube diagonal exactly
+  const double a = aniso_host(kind, e1, e2, 1, 1, 1);
+  best = std::min(best, a * a * (c_eta * a * a + 0.5));
+  amin = std::min(amin, a);
+  if (amin_out) *amin_out = amin;
+  return best;
+}
+
+}  // namespace
+
+struct lbpf_sim {
+  lbpf_grid g{};
+  lbpf_lattice lat{};
+  lbpf_params p{};
+  const KernelTable* kt = nullptr;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  long long nsite = 0;
+  void* pop[2][3] = {};
+  void* phi[3] = {};
+  void* U[2] = {};
+  void* th[2] = {};
+  SimDev hd{};
+  SimDev* dd = nullptr;
+  WorkItem* d_items = nullptr;
+  int nitems = 0;
+  int by = 16, zchunk = 0;
+  double* d_part = nullptr;  // reduction partials + 4 results
+  int npart = 0;
+  double* d_small = nullptr; // tip output
+  double* h_small = nullptr; // pinned
+  double* d_tmp = nullptr;   // FP64 staging (3 x nsite), allocated on demand
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_ok = false;
+  int64_t steps = 0;      // steps since the state was set; fixes buffer parity and phi level
+  int64_t step_base = 0;  // step count carried in from a checkpoint
+  int sticky = LBPF_OK;
+  double theta0 = 0.0, U0 = 0.0;
+  StepLaunch fphi = nullptr, futh = nullptr;
+  size_t smem_phi = 0, smem_uth = 0;
+};
+
+struct lbpf_batch {
+  std::vector<lbpf_sim*> sims;
+  cudaStream_t stream = nullptr;
+  SimDev* dd = nullptr;
+  WorkItem* d_items = nullptr;
+  int nitems = 0;
+  int by = 16;
+  StepLaunch fphi = nullptr, futh = nullptr;
+  size_t smem_phi = 0, smem_uth = 0;
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_ok = false;
+};
+
+#define CK(sim, call)                                  \
+  do {                                                 \
+    cudaError_t e__ = (call);                          \
+    if (e__ != cudaSuccess) {                          \
+      if (sim) (sim)->sticky = LBPF_ECUDA;             \
+      fprintf(stderr, "lbpf: CUDA error %s at %s:%d\n", cudaGetErrorString(e__), __FILE__, __LINE__); \
+      return LBPF_ECUDA;                               \
+    }                                                  \
+  } while (0)
+
+namespace {
+
+void build_items(int sim_index, int nx, int ny, int nz, int by, int zchunk, std::vector<WorkItem>& out) {
+  const int ty = by - 2;
+  for (int z0 = 0; z0 < nz; z0 += zchunk)
+    for (int y0 = 0; y0 < ny; y0 += ty)
+      for (int x0 = 0; x0 < nx; x0 += TILE_X) out.push_back(WorkItem{sim_index, x0, y0, z0, std::min(nz, z0 + zchunk)});
+}
+
+int default_zchunk(int nx, int ny, int nz, int by) {
+  const long long cols = (long long)((nx + TILE_X - 1) / TILE_X) * ((ny + by - 3) / (by - 2));
+  const long long target = 152LL * 8;  // enough blocks for several waves on 152 SMs
+  long long chunks = (target + cols - 1) / cols;
+  chunks = std::max(1LL, std::min(chunks, (long long)std::max(1, nz / 16)));
+  return (int)((nz + chunks - 1) / chunks);
+}
+
+// The dynamic shared-memory limit is an attribute of the kernel, shared by every
+// simulation that launches it: raise it once to the device's opt-in maximum so
+// that no handle's tiling can lower it under another handle's launches.
+int raise_smem_limit(const void* fn, int device) {
+  int maxsm = 0;
+  if (cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) return LBPF_ECUDA;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm) != cudaSuccess) return LBPF_ECUDA;
+  return LBPF_OK;
+}
+
+int set_smem_attrs(lbpf_sim* s) {
+  const KernelTable& t = *s->kt;
+  const int a = q_index(s->lat.q_phi), b = q_index(s->lat.q_u), c = qt_index(s->lat.q_theta);
+  if (raise_smem_limit(t.phi_fn[a], s->device) || raise_smem_limit(t.uth_fn[b][c], s->device)) {
+    s->sticky = LBPF_ECUDA;
+    return LBPF_ECUDA;
+  }
+  return LBPF_OK;
+}
+
+int apply_tiling(lbpf_sim* s, int by, int zchunk) {
+  const KernelTable& t = *s->kt;
+  s->by = by;
+  s->zchunk = zchunk > 0 ? zchunk : default_zchunk(s->g.nx, s->g.ny, s->g.nz, by);
+  s->smem_phi = phi_smem_bytes(t, s->lat.q_phi, by);
+  s->smem_uth = uth_smem_bytes(t, s->lat.q_u, s->lat.q_theta, by);
+  int maxsm = 0;
+  CK(s, cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device));
+  if ((int)s->smem_phi > maxsm || (int)s->smem_uth > maxsm) return LBPF_EINVAL;
+  std::vector<WorkItem> items;
+  build_items(0, s->g.nx, s->g.ny, s->g.nz, by, s->zchunk, items);
+  if (s->d_items) cudaFree(s->d_items);
+  s->d_items = nullptr;
+  CK(s, cudaMalloc(&s->d_items, items.size() * sizeof(WorkItem)));
+  CK(s, cudaMemcpy(s->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
+  s->nitems = (int)items.size();
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  s->gexec = nullptr;
+  s->graph_ok = false;
+  return set_smem_attrs(s);
+}
+
+int launch_step(cudaStream_t st, StepLaunch fphi, StepLaunch futh, int nitems, int by, size_t smem_phi,
+                size_t smem_uth, const SimDev* dd, const WorkItem* items, int s6) {
+  cudaError_t e = fphi(dim3(nitems), dim3(32, by), smem_phi, st, dd, items, s6);
+  if (e != cudaSuccess) return LBPF_ECUDA;
+  e = futh(dim3(nitems), dim3(32, by), smem_uth, st, dd, items, s6);
+  return e == cudaSuccess ? LBPF_OK : LBPF_ECUDA;
+}
+
+int capture_graph(cudaStream_t st, StepLaunch fphi, StepLaunch futh, int nitems, int by, size_t smem_phi,
+                  size_t smem_uth, const SimDev* dd, const WorkItem* items, cudaGraphExec_t* out) {
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LBPF_ECUDA;
+  int rc = LBPF_OK;
+  for (int s6 = 0; s6 < kGraphSteps && rc == LBPF_OK; ++s6)
+    rc = launch_step(st, fphi, futh, nitems, by, smem_phi, smem_uth, dd, items, s6);
+  cudaError_t e = cudaStreamEndCapture(st, &graph);
+  if (rc != LBPF_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return LBPF_ECUDA;
+  }
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  return e == cudaSuccess ? LBPF_OK : LBPF_ECUDA;
+}
+
+int ensure_tmp(lbpf_sim* s) {
+  if (s->d_tmp) return LBPF_OK;
+  if (cudaMalloc(&s->d_tmp, sizeof(double) * 3 * (size_t)s->nsite) != cudaSuccess) {
+    cudaGetLastError();
+    s->d_tmp = nullptr;
+    return LBPF_ENOMEM;
+  }
+  return LBPF_OK;
+}
+
+int validate(const lbpf_grid* g, const lbpf_lattice* l, const lbpf_params* p) {
+  if (!g || !l || !p) return LBPF_EINVAL;
+  if (g->nx < 1 || g->ny < 1 || g->nz < 1) return LBPF_EINVAL;
+  if ((long long)g->nx * g->ny > (1LL << 31) || (long long)g->nx * g->ny * g->nz > (1LL << 40)) return LBPF_EINVAL;
+  if (q_index(l->q_phi) < 0 || q_index(l->q_u) < 0 || qt_index(l->q_theta) < 0) return LBPF_EINVAL;
+  if (!(p->W0 > 0) || !(p->tau0 > 0) || !(p->D > 0) || !(p->dx > 0) || !(p->dt > 0)) return LBPF_EINVAL;
+  if (l->q_theta && !(p->kappa > 0)) return LBPF_EINVAL;
+  if (!(p->k > 0) || !(p->k <= 1)) return LBPF_EINVAL;
+  if (p->aniso != 0 && p->aniso != 1) return LBPF_EINVAL;
+  if (!table_for(p->storage)) return LBPF_EINVAL;
+  if (!isfinite(p->lambda) || !isfinite(p->Mc_inf) || !isfinite(p->eps1) || !isfinite(p->eps2)) return LBPF_EINVAL;
+  if (p->grad2_min < 0) return LBPF_EINVAL;
+  const double c_eta = p->W0 * p->W0 / p->tau0 * p->dt / (p->dx * p->dx) / lattice_e2(l->q_phi);
+  double amin = 0;
+  const double teff = min_effective_tau(p->aniso, p->eps1, p->eps2, c_eta, &amin);
+  if (!(amin > 0) || !(teff > 0.5)) return LBPF_EUNSTABLE;
+  return LBPF_OK;
+}
+
+void fill_dev(lbpf_sim* s) {
+  const lbpf_params& p = s->p;
+  SimDev& d = s->hd;
+  d.nx = s->g.nx; d.ny = s->g.ny; d.nz = s->g.nz;
+  d.q_theta = s->lat.q_theta;
+  d.nsite = s->nsite;
+  for (int b = 0; b < 2; ++b)
+    for (int f = 0; f < 3; ++f) d.pop[b][f] = s->pop[b][f];
+  for (int l = 0; l < 3; ++l) d.phi[l] = s->phi[l];
+  for (int b = 0; b < 2; ++b) { d.U[b] = s->U[b]; d.th[b] = s->th[b]; }
+  const double e2p = lattice_e2(s->lat.q_phi), e2u = lattice_e2(s->lat.q_u);
+  const double W2t = p.W0 * p.W0 / p.tau0;
+  d.inv2dx = 1.0 / (2.0 * p.dx);
+  d.c_eta = W2t * p.dt / (p.dx * p.dx) / e2p;
+  d.c_N = p.dt / p.dx * W2t / e2p;
+  d.dt_tau0 = p.dt / p.tau0;
+  d.lamM = p.lambda * p.Mc_inf;
+  d.lam = p.lambda;
+  d.eps1 = p.eps1; d.eps2 = p.eps2;
+  d.grad2_min = p.grad2_min > 0 ? p.grad2_min : 1e-12;
+  d.aniso = p.aniso;
+  d.antitrapping = p.antitrapping ? 1 : 0;
+  d.k = p.k;
+  d.inv_etaU = 1.0 / (p.D * p.dt / (p.dx * p.dx) / e2u + 0.5);
+  d.c_J = p.dt / p.dx / e2u;
+  d.D_dx2 = p.D / (p.dx * p.dx);
+  d.D = p.D;
+  d.at_amp = p.W0 / (2.0 * sqrt(2.0));
+  d.dt = p.dt;
+  d.inv_dt = 1.0 / p.dt;
+  d.inv_etaT = s->lat.q_theta ? 1.0 / (p.kappa * p.dt / (p.dx * p.dx) / lattice_e2(s->lat.q_theta) + 0.5) : 0.0;
+  d.theta0 = s->theta0;
+  d.shift_h = s->U0;
+  d.shift_f = s->theta0;
+  // codec scales: powers of two keeping the stored deviations well inside the FP16 range
+  for (int f = 0; f < 3; ++f) {
+    d.scale[f] = s->kt->shifted ? 4096.0 : 1.0;
+    d.inv_scale[f] = 1.0 / d.scale[f];
+  }
+}
+
+int upload_dev(lbpf_sim* s) {
+  fill_dev(s);
+  CK(s, cudaMemcpy(s->dd, &s->hd, sizeof(SimDev), cudaMemcpyHostToDevice));
+  return LBPF_OK;
+}
+
+void free_sim(lbpf_sim* s) {
+  if (!s) return;
+  for (int b = 0; b < 2; ++b)
+    for (int f = 0; f < 3; ++f) if (s->pop[b][f]) cudaFree(s->pop[b][f]);
+  for (int l = 0; l < 3; ++l) if (s->phi[l]) cudaFree(s->phi[l]);
+  for (int b = 0; b < 2; ++b) {
+    if (s->U[b]) cudaFree(s->U[b]);
+    if (s->th[b]) cudaFree(s->th[b]);
+  }
+  if (s->dd) cudaFree(s->dd);
+  if (s->d_items) cudaFree(s->d_items);
+  if (s->d_part) cudaFree(s->d_part);
+  if (s->d_small) cudaFree(s->d_small);
+  if (s->h_small) cudaFreeHost(s->h_small);
+  if (s->d_tmp) cudaFree(s->d_tmp);
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  delete s;
+}
+
+int aux_blocks_host(size_t n) {
+  size_t b = (n + 255) / 256;
+  return (int)std::max<size_t>(1, std::min<size_t>(b, 152 * 32));
+}
+
+inline int s6_of(const lbpf_sim* s) { return (int)(s->steps % kGraphSteps); }
+inline int par_of(const lbpf_sim* s) { return (int)(s->steps & 1); }
+
+}  // namespace
+
+extern "C" {
+
+const char* lbpf_strerror(int code) {
+  switch (code) {
+    case LBPF_OK: return "ok";
+    case LBPF_EINVAL: return "invalid argument";
+    case LBPF_EUNSTABLE: return "unstable parameters: a relaxation time a_s^2 eta <= 1/2";
+    case LBPF_ENOMEM: return "device allocation failed";
+    case LBPF_ENAN: return "non-finite value in the fields";
+    case LBPF_ETIMEOUT: return "bounded device wait timed out";
+    case LBPF_ECUDA: return "CUDA runtime error";
+    default: return "unknown error";
+  }
+}
+
+int lbpf_create(const lbpf_grid* grid, const lbpf_lattice* lattice, const lbpf_params* params, void* cuda_stream,
+                lbpf_sim** out) {
+  if (!out) return LBPF_EINVAL;
+  *out = nullptr;
+  int rc = validate(grid, lattice, params);
+  if (rc != LBPF_OK) return rc;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return LBPF_ECUDA;
+  }
+  lbpf_sim* s = new lbpf_sim();
+  s->g = *grid;
+  s->lat = *lattice;
+  s->p = *params;
+  s->kt = table_for(params->storage);
+  s->nsite = (long long)grid->nx * grid->ny * grid->nz;
+  if (cudaGetDevice(&s->device) != cudaSuccess) { free_sim(s); return LBPF_ECUDA; }
+  if (cuda_stream) {
+    s->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) { free_sim(s); return LBPF_ECUDA; }
+    s->own_stream = true;
+  }
+  const size_t N = (size_t)s->nsite;
+  const int qs[3] = {lattice->q_phi, lattice->q_u, lattice->q_theta};
+  bool ok = true;
+  for (int b = 0; b < 2 && ok; ++b)
+    for (int f = 0; f < 3 && ok; ++f)
+      if (qs[f]) ok = cudaMalloc(&s->pop[b][f], (size_t)qs[f] * N * s->kt->sbytes) == cudaSuccess;
+  for (int l = 0; l < 3 && ok; ++l) ok = cudaMalloc(&s->phi[l], N * s->kt->tbytes) == cudaSuccess;
+  for (int b = 0; b < 2 && ok; ++b) {
+    ok = cudaMalloc(&s->U[b], N * s->kt->tbytes) == cudaSuccess;
+    if (ok && lattice->q_theta) ok = cudaMalloc(&s->th[b], N * s->kt->tbytes) == cudaSuccess;
+  }
+  s->npart = 1024;
+  if (ok) ok = cudaMalloc(&s->d_part, sizeof(double) * (4 * s->npart + 8)) == cudaSuccess;
+  if (ok) ok = cudaMalloc(&s->d_small, sizeof(double) * 8) == cudaSuccess;
+  if (ok) ok = cudaMallocHost(&s->h_small, sizeof(double) * 8) == cudaSuccess;
+  if (ok) ok = cudaMalloc(&s->dd, sizeof(SimDev)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_sim(s);
+    return LBPF_ENOMEM;
+  }
+  // zero state until initialised
+  for (int b = 0; b < 2; ++b)
+    for (int f = 0; f < 3; ++f)
+      if (s->pop[b][f]) cudaMemsetAsync(s->pop[b][f], 0, (size_t)qs[f] * N * s->kt->sbytes, s->stream);
+  for (int l = 0; l < 3; ++l) cudaMemsetAsync(s->phi[l], 0, N * s->kt->tbytes, s->stream);
+  for (int b = 0; b < 2; ++b) {
+    cudaMemsetAsync(s->U[b], 0, N * s->kt->tbytes, s->stream);
+    if (s->th[b]) cudaMemsetAsync(s->th[b], 0, N * s->kt->tbytes, s->stream);
+  }
+  s->fphi = s->kt->phi[q_index(lattice->q_phi)];
+  s->futh = s->kt->uth[q_index(lattice->q_u)][qt_index(lattice->q_theta)];
+  const int by = std::min(16, std::max(4, grid->ny + 2));
+  if ((rc = upload_dev(s)) != LBPF_OK || (rc = apply_tiling(s, by, 0)) != LBPF_OK) {
+    free_sim(s);
+    return rc;
+  }
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) { free_sim(s); return LBPF_ECUDA; }
+  *out = s;
+  return LBPF_OK;
+}
+
+int lbpf_destroy(lbpf_sim* s) {
+  if (!s) return LBPF_EINVAL;
+  cudaStreamSynchronize(s->stream);
+  free_sim(s);
+  return LBPF_OK;
+}
+
+int64_t lbpf_steps_done(const lbpf_sim* s) { return s ? s->step_base + s->steps : -1; }
+
+int lbpf_init_seed(lbpf_sim* s, int32_t n, const double* centres, const double* radii, double U0, double theta0) {
+  if (!s || n < 1 || !centres || !radii) return LBPF_EINVAL;
+  if (s->sticky) return s->sticky;
+  for (int m = 0; m < n; ++m)
+    if (!isfinite(radii[m]) || !isfinite(centres[3 * m]) || !isfinite(centres[3 * m + 1]) ||
+        !isfinite(centres[3 * m + 2]))
+      return LBPF_EINVAL;
+  if (!isfinite(U0) || !isfinite(theta0)) return LBPF_EINVAL;
+  s->U0 = U0;
+  s->theta0 = theta0;
+  int rc = upload_dev(s);
+  if (rc) return rc;
+  double* d_seed = nullptr;
+  CK(s, cudaMalloc(&d_seed, sizeof(double) * 4 * n));
+  CK(s, cudaMemcpyAsync(d_seed, centres, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s->stream));
+  CK(s, cudaMemcpyAsync(d_seed + 3 * n, radii, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
+  const double c = s->p.dx / (sqrt(2.0) * s->p.W0);
+  // phi of the seeds into level 1 (scratch), populations at buffer 0, moments at level 0,
+  // and level 2 (phi^{n-1} of the codec) = the seed profile used by the encoder.
+  CK(s, s->kt->init_scalar(s->stream, s->g.nx, s->g.ny, s->g.nz, d_seed, d_seed + 3 * n, n, c, s->phi[1]));
+  const LatRT Lp = make_lat_rt(s->lat.q_phi), Lu = make_lat_rt(s->lat.q_u);
+  LatRT Lt{};
+  if (s->lat.q_theta) Lt = make_lat_rt(s->lat.q_theta);
+  CK(s, s->kt->init_pop(s->stream, s->hd, Lp, Lu, Lt, s->phi[1], U0, theta0));
+  CK(s, cudaMemcpyAsync(s->phi[2], s->phi[1], (size_t)s->nsite * s->kt->tbytes, cudaMemcpyDeviceToDevice, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  cudaFree(d_seed);
+  s->steps = 0;
+  s->step_base = 0;
+  return LBPF_OK;
+}
+
+int lbpf_step(lbpf_sim* s, int64_t n) {
+  if (!s || n < 0) return LBPF_EINVAL;
+  if (s->sticky) return s->sticky;
+  while (n > 0) {
+    if (s6_of(s) == 0 && n >= kGraphSteps) {
+      if (!s->graph_ok) {
+        if (s->gexec) cudaGraphExecDestroy(s->gexec);
+        s->gexec = nullptr;
+        if (capture_graph(s->stream, s->fphi, s->futh, s->nitems, s->by, s->smem_phi, s->smem_uth, s->dd,
+                          s->d_items, &s->gexec) != LBPF_OK) {
+          s->sticky = LBPF_ECUDA;
+          return LBPF_ECUDA;
+        }
+        s->graph_ok = true;
+      }
+      CK(s, cudaGraphLaunch(s->gexec, s->stream));
+      s->steps += kGraphSteps;
+      n -= kGraphSteps;
+    } else {
+      if (launch_step(s->stream, s->fphi, s->futh, s->nitems, s->by, s->smem_phi, s->smem_uth, s->dd, s->d_items,
+                      s6_of(s)) != LBPF_OK) {
+        s->sticky = LBPF_ECUDA;
+        return LBPF_ECUDA;
+      }
+      s->steps += 1;
+      n -= 1;
+    }
+  }
+  return LBPF_OK;
+}
+
+int lbpf_step_timed(lbpf_sim* s, int64_t n, double ms_kernels[3]) {
+  if (!s || n < 1 || !ms_kernels) return LBPF_EINVAL;
+  if (s->sticky) return s->sticky;
+  std::vector<cudaEvent_t> ev((size_t)(2 * n + 1));
+  for (auto& e : ev) CK(s, cudaEventCreate(&e));
+  CK(s, cudaEventRecord(ev[0], s->stream));
+  for (int64_t k = 0; k < n; ++k) {
+    const int s6 = s6_of(s);
+    CK(s, s->fphi(dim3(s->nitems), dim3(32, s->by), s->smem_phi, s->stream, s->dd, s->d_items, s6));
+    CK(s, cudaEventRecord(ev[2 * k + 1], s->stream));
+    CK(s, s->futh(dim3(s->nitems), dim3(32, s->by), s->smem_uth, s->stream, s->dd, s->d_items, s6));
+    CK(s, cudaEventRecord(ev[2 * k + 2], s->stream));
+    s->steps += 1;
+  }
+  CK(s, cudaEventSynchronize(ev[2 * n]));
+  double tp = 0, tu = 0;
+  for (int64_t k = 0; k < n; ++k) {
+    float a = 0, b = 0;
+    CK(s, cudaEventElapsedTime(&a, ev[2 * k], ev[2 * k + 1]));
+    CK(s, cudaEventElapsedTime(&b, ev[2 * k + 1], ev[2 * k + 2]));
+    tp += a;
+    tu += b;
+  }
+  float all = 0;
+  CK(s, cudaEventElapsedTime(&all, ev[0], ev[2 * n]));
+  for (auto& e : ev) cudaEventDestroy(e);
+  ms_kernels[0] = tp;
+  ms_kernels[1] = tu;
+  ms_kernels[2] = all;
+  return LBPF_OK;
+}
+
+int lbpf_read_fields(lbpf_sim* s, uint32_t mask, double* phi, double* U, double* theta) {
+  if (!s) return LBPF_EINVAL;
+  if (s->sticky) return s->sticky;
+  if (((mask & LBPF_PHI) && !phi) || ((mask & LBPF_U) && !U) || ((mask & LBPF_THETA) && !theta)) return LBPF_EINVAL;
+  const size_t N = (size_t)s->nsite;
+  const void* src[3] = {s->phi[s6_of(s) % 3], s->U[par_of(s)], s->lat.q_theta ? s->th[par_of(s)] : nullptr};
+  double* dst[3] = {(mask & LBPF_PHI) ? phi : nullptr, (mask & LBPF_U) ? U : nullptr,
+                    (mask & LBPF_THETA) ? theta : nullptr};
+  const bool need_tmp = s->kt->tbytes != 8;
+  if (need_tmp) {
+    int rc = ensure_tmp(s);
+    if (rc) return rc;
+  }
+  for (int f = 0; f < 3; ++f) {
+    if (!dst[f]) continue;
+    if (!src[f]) {
+      CK(s, cudaStreamSynchronize(s->stream));
+      for (size_t i = 0; i < N; ++i) dst[f][i] = s->theta0;
+      continue;
+    }
+    if (need_tmp) {
+      CK(s, s->kt->to_double(s->stream, s->d_tmp, src[f], (long long)N));
+      CK(s, cudaMemcpyAsync(dst[f], s->d_tmp, N * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    } else {
+      CK(s, cudaMemcpyAsync(dst[f], src[f], N * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    }
+    CK(s, cudaStreamSynchronize(s->stream));
+  }
+  return LBPF_OK;
+}
+
+int lbpf_sums(lbpf_sim* s, double out[4]) {
+  if (!s || !out) return LBPF_EINVAL;
+  if (s->sticky) return s->sticky;
+  const void* th = s->lat.q_theta ? s->th[par_of(s)] : nullptr;
+  const int nblk = (int)std::min<long long>(s->npart, std::max<long long>(1, (s->nsite + 255) / 256));
+  CK(s, s->kt->sums(s->stream, s->phi[s6_of(s) % 3], s->U[par_of(s)], th, s->theta0, s->p.k, s->nsite, s->d_part,
+                    nblk));
+  CK(s, cudaMemcpyAsync(s->h_small, s->d_part + 4 * nblk, 4 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  bool fin = true;
+  for (int c = 0; c < 4; ++c) {
+    out[c] = s->h_small[c];
+    fin = fin && isfinite(out[c]);
+  }
+  return fin ? LBPF_OK : LBPF_ENAN;
+}
+
+int lbpf_tip(lbpf_sim* s, const int32_t centre[3], double* x_tip, double* rho) {
+  if (!s || !centre || !x_tip) return LBPF_EINVAL;
+  if (s->sticky) return s->sticky;
+  CK(s, s->kt->tip(s->stream, s->phi[s6_of(s) % 3], s->g.nx, s->g.ny, s->g.nz, centre[0], centre[1], centre[2],
+                   s->d_small));
+  CK(s, cudaMemcpyAsync(s->h_small, s->d_small, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  *x_tip = s->h_small[0];
+  if (rho) *rho = s->h_small[1];
+  return LBPF_OK;
+}
+
+namespace {
+// Import post-streaming populations.  `moments` (optional, FP64, 4 x nsite):
+// phi^n, phi^{n-1}, U^n, theta^n to install instead of recomputing the moments
+// from the populations, so that a checkpoint restarts bit for bit.
+int import_state(lbpf_sim* s, const double* g, const double* h, const double* f, double theta0,
+                 const double* moments) {
+  int rc = ensure_tmp(s);
+  if (rc) return rc;
+  s->theta0 = theta0;
+  if ((rc = upload_dev(s))) return rc;
+  s->steps = 0;
+  s->step_base = 0;
+  const size_t N = (size_t)s->nsite;
+  double* acc = s->d_tmp;
+  double* b0 = s->d_tmp + N;
+  double* b1 = s->d_tmp + 2 * N;
+  const double* host[3] = {g, h, f};
+  const int qs[3] = {s->lat.q_phi, s->lat.q_u, s->lat.q_theta};
+  void* mom[3] = {s->phi[0], s->U[0], s->th[0]};
+  for (int fld = 0; fld < 3; ++fld) {
+    if (!qs[fld]) continue;
+    const LatRT L = make_lat_rt(qs[fld]);
+    if (moments) {
+      const double* m = moments + (size_t)(fld == 0 ? 0 : fld + 1) * N;
+      CK(s, cudaMemcpyAsync(acc, m, N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    } else {
+      // moments: sum over i in index order, in FP64
+      CK(s, cudaMemsetAsync(acc, 0, N * sizeof(double), s->stream));
+      for (int i = 0; i < qs[fld]; ++i) {
+        CK(s, cudaMemcpyAsync(b0, host[fld] + (size_t)i * N, N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+        k_acc<<<aux_blocks_host(N), 256, 0, s->stream>>>(acc, b0, (long long)N);
+        CK(s, cudaGetLastError());
+      }
+    }
+    CK(s, s->kt->from_double(s->stream, mom[fld], acc, (long long)N));
+    if (fld == 0) {
+      // codec reference phi^{n-1}: the saved level, or phi^n for an imported state
+      if (moments) {
+        CK(s, cudaMemcpyAsync(acc, moments + N, N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+        CK(s, s->kt->from_double(s->stream, s->phi[2], acc, (long long)N));
+      } else {
+        CK(s, cudaMemcpyAsync(s->phi[2], s->phi[0], N * s->kt->tbytes, cudaMemcpyDeviceToDevice, s->stream));
+      }
+    }
+    for (int i = 0; i < qs[fld]; ++i) {
+      const int j = L.opp[i];
+      if (j < i) continue;
+      CK(s, cudaMemcpyAsync(b0, host[fld] + (size_t)i * N, N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+      CK(s, cudaMemcpyAsync(b1, host[fld] + (size_t)j * N, N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+      CK(s, s->kt->pack(s->stream, s->hd, fld, 0, L, i, b0, b1, s->phi[2]));
+    }
+    CK(s, cudaStreamSynchronize(s->stream));
+  }
+  return LBPF_OK;
+}
+
+// Export phi^n, phi^{n-1}, U^n, theta^n as FP64 (4 x nsite).
+int export_moments(lbpf_sim* s, double* out) {
+  int rc = ensure_tmp(s);
+  if (rc) return rc;
+  const size_t N = (size_t)s->nsite;
+  const void* src[4] = {s->phi[s6_of(s) % 3], s->phi[(s6_of(s) + 2) % 3], s->U[par_of(s)],
+                        s->lat.q_theta ? s->th[par_of(s)] : nullptr};
+  for (int k = 0; k < 4; ++k) {
+    if (!src[k]) {
+      for (size_t i = 0; i < N; ++i) out[k * N + i] = s->theta0;
+      continue;
+    }
+    CK(s, s->kt->to_double(s->stream, s->d_tmp, src[k], (long long)N));
+    CK(s, cudaMemcpyAsync(out + k * N, s->d_tmp, N * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+  }
+  return LBPF_OK;
+}
+}  // namespace
+
+int lbpf_set_state(lbpf_sim* s, const double* g, const double* h, const double* f, double theta0) {
+  if (!s || !g || !h || (s->lat.q_theta && !f)) return LBPF_EINVAL;
+  if (s->sticky) return s->sticky;
+  return import_state(s, g, h, f, theta0, nullptr);
+}
+
+int lbpf_get_state(lbpf_sim* s, double* g, double* h, double* f) {
+  if (!s) return LBPF_EINVAL;
+  if (s->sticky) return s->sticky;
+  int rc = ensure_tmp(s);
+  if (rc) return rc;
+  const size_t N = (size_t)s->nsite;
+  double* b0 = s->d_tmp + N;
+  double* b1 = s->d_tmp + 2 * N;
+  double* host[3] = {g, h, f};
+  const int qs[3] = {s->lat.q_phi, s->lat.q_u, s->lat.q_theta};
+  const void* phi_prev = s->phi[(s6_of(s) + 2) % 3];
+  for (int fld = 0; fld < 3; ++fld) {
+    if (!qs[fld] || !host[fld]) continue;
+    const LatRT L = make_lat_rt(qs[fld]);
+    for (int i = 0; i < qs[fld]; ++i) {
+      const int j = L.opp[i];
+      if (j < i) continue;
+      CK(s, s->kt->unpack(s->stream, s->hd, fld, par_of(s), L, i, b0, b1, phi_prev));
+      CK(s, cudaMemcpyAsync(host[fld] + (size_t)i * N, b0, N * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+      if (j != i)
+        CK(s, cudaMemcpyAsync(host[fld] + (size_t)j * N, b1, N * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+      CK(s, cudaStreamSynchronize(s->stream));
+    }
+  }
+  return LBPF_OK;
+}
+
+int lbpf_set_tiling(lbpf_sim* s, int32_t by, int32_t zchunk) {
+  if (!s || by < 0 || zchunk < 0 || (by && (by < 4 || by > 16))) return LBPF_EINVAL;
+  if (s->sticky) return s->sticky;
+  CK(s, cudaStreamSynchronize(s->stream));
+  return apply_tiling(s, by ? by : s->by, zchunk ? zchunk : (by ? 0 : s->zchunk));
+}
+
+int lbpf_get_tiling(const lbpf_sim* s, int32_t* by, int32_t* zchunk) {
+  if (!s) return LBPF_EINVAL;
+  if (by) *by = s->by;
+  if (zchunk) *zchunk = s->zchunk;
+  return LBPF_OK;
+}
+
+int lbpf_autotune(lbpf_sim* s, int32_t steps, double* best_ms) {
+  if (!s || steps < 1) return LBPF_EINVAL;
+  if (s->sticky) return s->sticky;
+  CK(s, cudaStreamSynchronize(s->stream));
+  // snapshot of the current state: populations at the current buffer, all phi levels, U, theta
+  const size_t N = (size_t)s->nsite;
+  const int qs[3] = {s->lat.q_phi, s->lat.q_u, s->lat.q_theta};
+  std::vector<std::pair<void*, size_t>> live;
+  const int par = par_of(s);
+  for (int f = 0; f < 3; ++f)
+    if (qs[f]) live.push_back({s->pop[par][f], (size_t)qs[f] * N * s->kt->sbytes});
+  for (int l = 0; l < 3; ++l) live.push_back({s->phi[l], N * s->kt->tbytes});
+  live.push_back({s->U[par], N * s->kt->tbytes});
+  if (s->th[par]) live.push_back({s->th[par], N * s->kt->tbytes});
+  std::vector<void*> snap(live.size(), nullptr);
+  for (size_t k = 0; k < live.size(); ++k) {
+    if (cudaMalloc(&snap[k], live[k].second) != cudaSuccess) {
+      cudaGetLastError();
+      for (void* p : snap) if (p) cudaFree(p);
+      return LBPF_ENOMEM;
+    }
+    CK(s, cudaMemcpyAsync(snap[k], live[k].first, live[k].second, cudaMemcpyDeviceToDevice, s->stream));
+  }
+  const int64_t steps0 = s->steps;
+  const int by0 = s->by, zc0 = s->zchunk;
+  cudaEvent_t e0, e1;
+  CK(s, cudaEventCreate(&e0));
+  CK(s, cudaEventCreate(&e1));
+  double best = 1e300;
+  int bbest = by0, zbest = zc0;
+  const int bys[] = {8, 12, 16};
+  for (int by : bys) {
+    if (by > s->g.ny + 2 && by != bys[0]) continue;
+    const int zdef = default_zchunk(s->g.nx, s->g.ny, s->g.nz, by);
+    const int zcs[] = {zdef, std::max(8, zdef / 2), std::min(s->g.nz, zdef * 2), s->g.nz};
+    for (int zc : zcs) {
+      if (apply_tiling(s, by, zc) != LBPF_OK) { s->sticky = LBPF_OK; continue; }
+      int rc = lbpf_step(s, 1);  // warm-up
+      CK(s, cudaEventRecord(e0, s->stream));
+      if (rc == LBPF_OK) rc = lbpf_step(s, steps);
+      CK(s, cudaEventRecord(e1, s->stream));
+      CK(s, cudaEventSynchronize(e1));
+      float ms = 0;
+      CK(s, cudaEventElapsedTime(&ms, e0, e1));
+      if (rc == LBPF_OK && ms / steps < best) {
+        best = ms / steps;
+        bbest = by;
+        zbest = zc;
+      }
+      // restore the snapshot and the step counter
+      for (size_t k = 0; k < live.size(); ++k) {
+        void* dst = live[k].first;
+        // populations of the current parity live in pop[par] (the counter is reset below)
+        CK(s, cudaMemcpyAsync(dst, snap[k], live[k].second, cudaMemcpyDeviceToDevice, s->stream));
+      }
+      s->steps = steps0;
+      CK(s, cudaStreamSynchronize(s->stream));
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (void* p : snap) cudaFree(p);
+  int rc = apply_tiling(s, bbest, zbest);
+  if (best_ms) *best_ms = best;
+  return rc;
+}
+
+// ---------------------------------------------------------------- checkpoint
+
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int32_t version;
+  lbpf_grid grid;
+  lbpf_lattice lat;
+  lbpf_params params;
+  int64_t steps;
+  double U0, theta0;
+};
+}  // namespace
+
+int lbpf_save(lbpf_sim* s, const char* path) {
+  if (!s || !path) return LBPF_EINVAL;
+  if (s->sticky) return s->sticky;
+  const size_t N = (size_t)s->nsite;
+  const int qs[3] = {s->lat.q_phi, s->lat.q_u, s->lat.q_theta};
+  std::vector<double> buf[3];
+  for (int f = 0; f < 3; ++f) buf[f].resize((size_t)qs[f] * N);
+  int rc = lbpf_get_state(s, buf[0].data(), buf[1].data(), qs[2] ? buf[2].data() : nullptr);
+  if (rc) return rc;
+  std::vector<double> mom(4 * N);
+  if ((rc = export_moments(s, mom.data()))) return rc;
+  FILE* fp = fopen(path, "wb");
+  if (!fp) return LBPF_EINVAL;
+  CkptHeader hdr{};
+  memcpy(hdr.magic, "LBPFCKP2", 8);
+  hdr.version = 2;
+  hdr.grid = s->g;
+  hdr.lat = s->lat;
+  hdr.params = s->p;
+  hdr.steps = s->step_base + s->steps;
+  hdr.U0 = s->U0;
+  hdr.theta0 = s->theta0;
+  bool ok = fwrite(&hdr, sizeof(hdr), 1, fp) == 1;
+  for (int f = 0; f < 3 && ok; ++f)
+    if (qs[f]) ok = fwrite(buf[f].data(), sizeof(double), buf[f].size(), fp) == buf[f].size();
+  if (ok) ok = fwrite(mom.data(), sizeof(double), mom.size(), fp) == mom.size();
+  ok = (fclose(fp) == 0) && ok;
+  return ok ? LBPF_OK : LBPF_EINVAL;
+}
+
+int lbpf_load(lbpf_sim* s, const char* path) {
+  if (!s || !path) return LBPF_EINVAL;
+  if (s->sticky) return s->sticky;
+  FILE* fp = fopen(path, "rb");
+  if (!fp) return LBPF_EINVAL;
+  CkptHeader hdr{};
+  if (fread(&hdr, sizeof(hdr), 1, fp) != 1 || memcmp(hdr.magic, "LBPFCKP2", 8) != 0 ||
+      memcmp(&hdr.grid, &s->g, sizeof(lbpf_grid)) != 0 || memcmp(&hdr.lat, &s->lat, sizeof(lbpf_lattice)) != 0) {
+    fclose(fp);
+    return LBPF_EINVAL;
+  }
+  const size_t N = (size_t)s->nsite;
+  const int qs[3] = {s->lat.q_phi, s->lat.q_u, s->lat.q_theta};
+  std::vector<double> buf[3];
+  bool ok = true;
+  for (int f = 0; f < 3 && ok; ++f) {
+    buf[f].resize((size_t)qs[f] * N);
+    if (qs[f]) ok = fread(buf[f].data(), sizeof(double), buf[f].size(), fp) == buf[f].size();
+  }
+  std::vector<double> mom(4 * N);
+  if (ok) ok = fread(mom.data(), sizeof(double), mom.size(), fp) == mom.size();
+  fclose(fp);
+  if (!ok) return LBPF_EINVAL;
+  s->U0 = hdr.U0;
+  int rc = import_state(s, buf[0].data(), buf[1].data(), qs[2] ? buf[2].data() : nullptr, hdr.theta0, mom.data());
+  if (rc) return rc;
+  s->steps = 0;  // buffer phase restarts at 0
+  s->step_base = hdr.steps;
+  return LBPF_OK;
+}
+
+// ---------------------------------------------------------------- batch
+
+int lbpf_batch_create(int32_t n, lbpf_sim* const* sims, void* cuda_stream, lbpf_batch** out) {
+  if (!out || n < 1 || !sims) return LBPF_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!sims[i]) return LBPF_EINVAL;
+    if (sims[i]->sticky) return sims[i]->sticky;
+    if (memcmp(&sims[i]->lat, &sims[0]->lat, sizeof(lbpf_lattice)) != 0 || sims[i]->p.storage != sims[0]->p.storage ||
+        sims[i]->device != sims[0]->device)
+      return LBPF_EINVAL;
+  }
+  lbpf_batch* b = new lbpf_batch();
+  b->sims.assign(sims, sims + n);
+  b->stream = cuda_stream ? (cudaStream_t)cuda_stream : sims[0]->stream;
+  const KernelTable& t = *sims[0]->kt;
+  b->by = 16;
+  std::vector<WorkItem> items;
+  std::vector<SimDev> descs;
+  for (int i = 0; i < n; ++i) {
+    lbpf_sim* s = sims[i];
+    cudaStreamSynchronize(s->stream);
+    fill_dev(s);
+    descs.push_back(s->hd);
+    build_items(i, s->g.nx, s->g.ny, s->g.nz, b->by, default_zchunk(s->g.nx, s->g.ny, s->g.nz, b->by), items);
+  }
+  // interleave large and small simulations: sort items by descending z-chunk work
+  std::stable_sort(items.begin(), items.end(),
+                   [](const WorkItem& a, const WorkItem& c) { return (a.z1 - a.z0) > (c.z1 - c.z0); });
+  b->nitems = (int)items.size();
+  b->fphi = sims[0]->fphi;
+  b->futh = sims[0]->futh;
+  b->smem_phi = phi_smem_bytes(t, sims[0]->lat.q_phi, b->by);
+  b->smem_uth = uth_smem_bytes(t, sims[0]->lat.q_u, sims[0]->lat.q_theta, b->by);
+  bool ok = cudaMalloc(&b->dd, descs.size() * sizeof(SimDev)) == cudaSuccess &&
+            cudaMalloc(&b->d_items, items.size() * sizeof(WorkItem)) == cudaSuccess;
+  ok = ok && cudaMemcpy(b->dd, descs.data(), descs.size() * sizeof(SimDev), cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice) == cudaSuccess;
+  const int a = q_index(sims[0]->lat.q_phi), qb = q_index(sims[0]->lat.q_u), qc = qt_index(sims[0]->lat.q_theta);
+  ok = ok && raise_smem_limit(t.phi_fn[a], sims[0]->device) == LBPF_OK;
+  ok = ok && raise_smem_limit(t.uth_fn[qb][qc], sims[0]->device) == LBPF_OK;
+  if (!ok) {
+    cudaGetLastError();
+    lbpf_batch_destroy(b);
+    return LBPF_ENOMEM;
+  }
+  *out = b;
+  return LBPF_OK;
+}
+
+int lbpf_batch_step(lbpf_batch* b, int64_t n) {
+  if (!b || n < 0) return LBPF_EINVAL;
+  const int64_t st0 = b->sims[0]->steps;
+  for (lbpf_sim* s : b->sims) {
+    if (s->sticky) return s->sticky;
+    if (s->steps != st0) return LBPF_EINVAL;  // batch members advance in lockstep
+  }
+  int64_t steps = st0;
+  while (n > 0) {
+    const int s6 = (int)(steps % kGraphSteps);
+    if (s6 == 0 && n >= kGraphSteps) {
+      if (!b->graph_ok) {
+        if (capture_graph(b->stream, b->fphi, b->futh, b->nitems, b->by, b->smem_phi, b->smem_uth, b->dd, b->d_items,
+                          &b->gexec) != LBPF_OK)
+          return LBPF_ECUDA;
+        b->graph_ok = true;
+      }
+      if (cudaGraphLaunch(b->gexec, b->stream) != cudaSuccess) return LBPF_ECUDA;
+      steps += kGraphSteps;
+      n -= kGraphSteps;
+    } else {
+      if (launch_step(b->stream, b->fphi, b->futh, b->nitems, b->by, b->smem_phi, b->smem_uth, b->dd, b->d_items, s6) !=
+          LBPF_OK)
+        return LBPF_ECUDA;
+      steps += 1;
+      n -= 1;
+    }
+  }
+  for (lbpf_sim* s : b->sims) s->steps = steps;
+  return LBPF_OK;
+}
+
+int lbpf_batch_destroy(lbpf_batch* b) {
+  if (!b) return LBPF_EINVAL;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->dd) cudaFree(b->dd);
+  if (b->d_items) cudaFree(b->d_items);
+  delete b;
+  return LBPF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,53 @@
+// lbpf_table.h -- per-storage table of kernel launchers (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbpf_dev.cuh"
+
+namespace lbpf {
+
+struct LatRT;
+
+using StepLaunch = cudaError_t (*)(dim3 grid, dim3 block, size_t smem, cudaStream_t st, const SimDev* sims,
+                                   const WorkItem* items, int s6);
+
+struct KernelTable {
+  int sbytes;            // bytes per stored population
+  int tbytes;            // bytes of the compute type
+  bool shifted;          // FP16/BF16 codec
+  StepLaunch phi[3];     // q_phi = 7, 15, 19
+  StepLaunch uth[3][4];  // q_u = 7, 15, 19  x  q_theta = 0, 7, 15, 19
+  const void* phi_fn[3];
+  const void* uth_fn[3][4];
+  cudaError_t (*init_scalar)(cudaStream_t, int nx, int ny, int nz, const double* cen, const double* rad, int nseed,
+                             double c, void* out);
+  cudaError_t (*init_pop)(cudaStream_t, const SimDev& sd, const LatRT& Lp, const LatRT& Lu, const LatRT& Lt,
+                          const void* phi0, double U0, double theta0);
+  cudaError_t (*pack)(cudaStream_t, const SimDev& sd, int field, int par, const LatRT& L, int i, const double* gi,
+                      const double* gj, const void* phi_prev);
+  cudaError_t (*unpack)(cudaStream_t, const SimDev& sd, int field, int par, const LatRT& L, int i, double* gi,
+                        double* gj, const void* phi_prev);
+  cudaError_t (*to_double)(cudaStream_t, double* out, const void* in, long long n);
+  cudaError_t (*from_double)(cudaStream_t, void* out, const double* in, long long n);
+  cudaError_t (*sums)(cudaStream_t, const void* phi, const void* U, const void* th, double theta0, double k,
+                      long long n, double* part, int nblk);
+  cudaError_t (*tip)(cudaStream_t, const void* phi, int nx, int ny, int nz, int cx, int cy, int cz, double* out);
+};
+
+const KernelTable& table_f64();
+const KernelTable& table_f32();
+const KernelTable& table_f16();
+const KernelTable& table_bf16();
+
+// shared-memory bytes of the step kernels for a block of 32 x by threads
+inline size_t phi_smem_bytes(const KernelTable& t, int qp, int by) {
+  const size_t rs = 34u * (size_t)(by + 2);
+  return ((t.shifted ? 6 : 3) * rs + (size_t)qp * 32u * by) * t.tbytes;
+}
+inline size_t uth_smem_bytes(const KernelTable& t, int qu, int qt, int by) {
+  const size_t rs = 34u * (size_t)(by + 2);
+  return (3 * rs + (size_t)(qu + qt) * 32u * by) * t.tbytes;
+}
+
+}  // namespace lbpf
