@@ -175,6 +175,35 @@ int lbpf_batch_create(int32_t n, lbpf_sim* const* sims, void* cuda_stream, lbpf_
 int lbpf_batch_step(lbpf_batch* batch, int64_t n_steps);
 int lbpf_batch_destroy(lbpf_batch* batch);
 
+/* Largest n_sites that lbpf_field_sums_noalloc accepts (65536 partial sums of
+ * 4096 sites each). */
+#define LBPF_NOALLOC_MAX_SITES (268435456LL)
+
+/* The same four FP64 sums as lbpf_sums, over caller-owned DEVICE arrays, with
+ * no memory allocation at all.  The paper has no counterpart: this serves
+ * callers that hold device fields but cannot call cudaMalloc -- code running
+ * while a stream is captured (allocation is not allowed there), loops that
+ * must avoid the implicit device synchronisation of cudaMalloc/cudaFree, and
+ * hosts whose device memory is fully reserved by another allocator.
+ *   phi, U, theta: device arrays of n_sites elements of the compute type of
+ *     `storage` (double for LBPF_F64, float otherwise); theta may be NULL, then
+ *     theta0 is used at every site.
+ *   k: partition coefficient of the solute sum.  out: HOST array of 4 doubles.
+ *   cuda_stream: stream to run on (NULL = legacy default stream); the call
+ *     synchronises it before returning.
+ * The reduction scratch (2 MiB) is a file-scope device array that every GPU
+ * loading the library keeps until the process exits; all calls on a device
+ * share it and each call overwrites the part it uses, so nothing in it needs
+ * clearing.  Calls that overlap on the GPU (several streams or host threads at
+ * once) race on that scratch and must be serialised by the caller.  The first
+ * call on a device looks up the scratch's device address with
+ * cudaGetSymbolAddress; make that first call before any stream capture.
+ * Returns LBPF_EINVAL for NULL inputs, n_sites < 1 or
+ * n_sites > LBPF_NOALLOC_MAX_SITES, LBPF_ENAN when a sum is not finite,
+ * LBPF_ECUDA on a CUDA error. */
+int lbpf_field_sums_noalloc(const void* phi, const void* U, const void* theta, int32_t storage, int64_t n_sites,
+                            double k, double theta0, double out[4], void* cuda_stream);
+
 /* Static description of an error code. */
 const char* lbpf_strerror(int code);
 
