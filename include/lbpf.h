@@ -60,7 +60,7 @@ extern "C" {
 #define LBPF_THETA 4u
 
 typedef struct {
-  int32_t nx, ny, nz; /* nodes per edge, each >= 1 */
+  int32_t nx, ny, nz; /* nodes per edge, each >= 1; nx*ny*nz < 2^32 / 19 (226,050,910) */
 } lbpf_grid;
 
 typedef struct {
@@ -152,10 +152,11 @@ int64_t lbpf_steps_done(const lbpf_sim* sim);
 int lbpf_save(lbpf_sim* sim, const char* path);
 int lbpf_load(lbpf_sim* sim, const char* path);
 
-/* Tiling of the step kernels: block rows `by` (4..32, block is 32 x by
- * threads) and z-chunk length (>= 1; the z range is split into chunks that are
- * processed by separate thread blocks).  0 keeps the current value.  Takes
- * effect at the next lbpf_step (the step graph is re-captured). */
+/* Tiling of the step kernels: node rows per block `by` (4..16; a block is
+ * 32 x by threads, one node per thread and plane) and z-chunk length
+ * (>= 1; the z range is split into chunks processed by separate thread
+ * blocks).  0 keeps the current value.  Takes effect at the next lbpf_step
+ * (the step graph is re-captured). */
 int lbpf_set_tiling(lbpf_sim* sim, int32_t by, int32_t zchunk);
 int lbpf_get_tiling(const lbpf_sim* sim, int32_t* by, int32_t* zchunk);
 

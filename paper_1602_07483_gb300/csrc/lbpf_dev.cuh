@@ -16,11 +16,14 @@
 // collision is then A_i(x) itself for every non-boundary node.
 //
 // Each thread block owns a 30 x (BY-2) column of the xy plane and marches in z
-// over a chunk of planes.  For every plane it recomputes the collisions on a
-// one-node halo (32 x BY nodes), keeps them in shared memory and gathers the
-// streamed populations of its interior columns into the zeroth moment of the
-// next step, so the moment fields cost one scalar write per node and the
-// distributions are read once and written once.
+// over a chunk of planes; a block is 32 x BY threads, one node per thread and
+// plane.  For every plane the block recomputes the
+// collisions on a one-node halo (32 x BY nodes) and gathers the streamed
+// populations of its interior nodes into the zeroth moment of the next step:
+// populations with e_y = 0 come from the thread itself or its x-neighbour lane
+// by warp shuffle, the others through a double-buffered shared-memory plane, so
+// each plane needs a single barrier.  The moment fields cost one scalar write
+// per node and the distributions are read once and written once.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -48,25 +51,40 @@ struct Lat<7> {
   __host__ __device__ static constexpr double B(int i) { return i == 0 ? -0.75 : 0.125; }
 };
 
+// The accessors are switch expressions so that, with the population loops
+// unrolled, every lookup folds to an immediate.
 template <>
 struct Lat<15> {
   static constexpr double e2 = 1.0 / 3.0;
-  // rows: e_0..e_6 as D3Q7, then the cube diagonals
+  // e_0..e_6 as D3Q7, then the cube diagonals
   __host__ __device__ static constexpr int ex(int i) {
-    constexpr int v[15] = {0, 1, 0, -1, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
-    return v[i];
+    switch (i) {
+      case 1: case 7: case 10: case 11: case 14: return 1;
+      case 3: case 8: case 9: case 12: case 13: return -1;
+      default: return 0;
+    }
   }
   __host__ __device__ static constexpr int ey(int i) {
-    constexpr int v[15] = {0, 0, 1, 0, -1, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1};
-    return v[i];
+    switch (i) {
+      case 2: case 7: case 8: case 11: case 12: return 1;
+      case 4: case 9: case 10: case 13: case 14: return -1;
+      default: return 0;
+    }
   }
   __host__ __device__ static constexpr int ez(int i) {
-    constexpr int v[15] = {0, 0, 0, 0, 0, 1, -1, 1, 1, 1, 1, -1, -1, -1, -1};
-    return v[i];
+    switch (i) {
+      case 5: case 7: case 8: case 9: case 10: return 1;
+      case 6: case 11: case 12: case 13: case 14: return -1;
+      default: return 0;
+    }
   }
   __host__ __device__ static constexpr int opp(int i) {
-    constexpr int v[15] = {0, 3, 4, 1, 2, 6, 5, 13, 14, 11, 12, 9, 10, 7, 8};
-    return v[i];
+    switch (i) {
+      case 1: return 3; case 2: return 4; case 3: return 1; case 4: return 2; case 5: return 6; case 6: return 5;
+      case 7: return 13; case 8: return 14; case 9: return 11; case 10: return 12;
+      case 11: return 9; case 12: return 10; case 13: return 7; case 14: return 8;
+      default: return 0;
+    }
   }
   __host__ __device__ static constexpr double w(int i) {
     return i == 0 ? 2.0 / 9.0 : (i <= 6 ? 1.0 / 9.0 : 1.0 / 72.0);
@@ -79,21 +97,36 @@ struct Lat<15> {
 template <>
 struct Lat<19> {
   static constexpr double e2 = 1.0 / 3.0;
+  // e_0..e_6 as D3Q7, then the twelve edge diagonals
   __host__ __device__ static constexpr int ex(int i) {
-    constexpr int v[19] = {0, 1, 0, -1, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
-    return v[i];
+    switch (i) {
+      case 1: case 7: case 9: case 11: case 13: return 1;
+      case 3: case 8: case 10: case 12: case 14: return -1;
+      default: return 0;
+    }
   }
   __host__ __device__ static constexpr int ey(int i) {
-    constexpr int v[19] = {0, 0, 1, 0, -1, 0, 0, 1, 1, -1, -1, 0, 0, 0, 0, 1, -1, 1, -1};
-    return v[i];
+    switch (i) {
+      case 2: case 7: case 8: case 15: case 17: return 1;
+      case 4: case 9: case 10: case 16: case 18: return -1;
+      default: return 0;
+    }
   }
   __host__ __device__ static constexpr int ez(int i) {
-    constexpr int v[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1};
-    return v[i];
+    switch (i) {
+      case 5: case 11: case 12: case 15: case 16: return 1;
+      case 6: case 13: case 14: case 17: case 18: return -1;
+      default: return 0;
+    }
   }
   __host__ __device__ static constexpr int opp(int i) {
-    constexpr int v[19] = {0, 3, 4, 1, 2, 6, 5, 10, 9, 8, 7, 14, 13, 12, 11, 18, 17, 16, 15};
-    return v[i];
+    switch (i) {
+      case 1: return 3; case 2: return 4; case 3: return 1; case 4: return 2; case 5: return 6; case 6: return 5;
+      case 7: return 10; case 8: return 9; case 9: return 8; case 10: return 7;
+      case 11: return 14; case 12: return 13; case 13: return 12; case 14: return 11;
+      case 15: return 18; case 16: return 17; case 17: return 16; case 18: return 15;
+      default: return 0;
+    }
   }
   __host__ __device__ static constexpr double w(int i) {
     return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
@@ -103,6 +136,31 @@ struct Lat<19> {
   }
 };
 // A_i = 1 for the rest population and 0 otherwise on all three lattices.
+
+// Populations with e_y != 0 cross block rows during the moment gather and go
+// through shared memory; yslot(i) numbers them 0..NY-1 (-1 for e_y = 0).
+template <int Q>
+struct YSlots {
+  __host__ __device__ static constexpr int count() {
+    int c = 0;
+    for (int i = 0; i < Q; ++i) c += Lat<Q>::ey(i) != 0;
+    return c;
+  }
+  __host__ __device__ static constexpr int slot(int i) {
+    if (Lat<Q>::ey(i) == 0) return -1;
+    int c = 0;
+    for (int j = 0; j < i; ++j) c += Lat<Q>::ey(j) != 0;
+    return c;
+  }
+};
+template <int Q>
+struct NYOf {
+  static constexpr int value = YSlots<Q>::count();
+};
+template <>
+struct NYOf<0> {
+  static constexpr int value = 0;
+};
 
 // ---------------------------------------------------------------- storage codec
 // FP64/FP32: stored as is.  FP16/BF16: stored = (f - shift) * scale, decoded to
@@ -188,7 +246,7 @@ constexpr int TILE_X = 30;  // interior columns per block row (block x = 32)
 // Eq. (Derivees_As); kind 1: Eq. (As_K41-K61) with its analytic derivatives.
 template <typename T>
 __device__ __forceinline__ T aniso_N(int kind, T e1, T e2, T gx, T gy, T gz, T G2, T& Nx, T& Ny, T& Nz) {
-  const T iG = (sizeof(T) == 8) ? T(1) / sqrt(G2) : rsqrtf((float)G2);
+  const T iG = (sizeof(T) == 8) ? T(1) / sqrt(G2) : (T)rsqrtf((float)G2);
   const T nx = gx * iG, ny = gy * iG, nz = gz * iG;
   const T x2 = nx * nx, y2 = ny * ny, z2 = nz * nz;
   const T s4 = x2 * x2 + y2 * y2 + z2 * z2;
@@ -216,42 +274,77 @@ __device__ __forceinline__ T aniso_N(int kind, T e1, T e2, T gx, T gy, T gz, T G
   return as;
 }
 
-__device__ __forceinline__ int ring_slot(int z) { return ((z % 3) + 3) % 3; }
+// Read-only (non-coherent) load: the distributions read by a step kernel are
+// never written by the same launch.
+template <typename S>
+__device__ __forceinline__ S ldro(const S* p) { return __ldg(p); }
 
-// Load plane z (clamped to the domain = mirror ghost at distance 1) of a scalar
-// field into a ring slot covering the block region plus one node of halo.
-template <typename T>
-__device__ __forceinline__ void load_ring(T* __restrict__ dst, const T* __restrict__ src, int z, int x0, int y0,
-                                          int nx, int ny, int nz, int RW, int RS, int tid, int nthr) {
-  const int zc = min(max(z, 0), nz - 1);
-  const long long base = (long long)zc * ny * nx;
-  for (int idx = tid; idx < RS; idx += nthr) {
-    const int ly = idx / RW;
-    const int lx = idx - ly * RW;
-    const int gx = min(max(x0 - 2 + lx, 0), nx - 1);
-    const int gy = min(max(y0 - 2 + ly, 0), ny - 1);
-    dst[idx] = src[base + (long long)gy * nx + gx];
+__device__ __forceinline__ int slot4(int z) { return (z + 4) & 3; }  // z >= -1
+
+// 1/x: IEEE division in FP64, the hardware approximate reciprocal in FP32
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+
+// Scalar-field ring: four planes of (BY + 2) x 34 values around the block
+// region (mirror ghosts by clamping).  Each thread owns up to RPT elements of a
+// plane; their in-plane offsets are computed once, and the plane two ahead of
+// the collision plane is fetched into registers one iteration early.
+constexpr int RPT = 2;  // 34 x (BY + 2) <= RPT x 32 x BY for BY >= 3
+
+struct RingMap {
+  int off[RPT];  // in-plane offset (y * nx + x), or -1 when the slot is unused
+  __device__ __forceinline__ void init(int x0, int y0, int nx, int ny, int RW, int RS, int tid, int nthr) {
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int idx = tid + r * nthr;
+      off[r] = -1;
+      if (idx < RS) {
+        const int ly = idx / RW;
+        const int lx = idx - ly * RW;
+        const int gx = min(max(x0 - 2 + lx, 0), nx - 1);
+        const int gy = min(max(y0 - 2 + ly, 0), ny - 1);
+        off[r] = gy * nx + gx;
+      }
+    }
   }
-}
+};
+
+template <typename T>
+struct RingRegs {
+  T v[RPT];
+  __device__ __forceinline__ void fetch(const RingMap& m, const T* __restrict__ src, int z, int nz, long long plane) {
+    const T* p = src + (long long)min(max(z, 0), nz - 1) * plane;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+      if (m.off[r] >= 0) v[r] = ldro(p + m.off[r]);
+  }
+  __device__ __forceinline__ void store(const RingMap& m, T* __restrict__ dst, int tid, int nthr) const {
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+      if (m.off[r] >= 0) dst[tid + r * nthr] = v[r];
+  }
+};
 
 // ---------------------------------------------------------------- phase field
 template <int QP, typename S>
 __global__ void __launch_bounds__(512) k_phi(const SimDev* __restrict__ sims, const WorkItem* __restrict__ items,
-                                             int s6) {
+                                                int s6) {
   using C = Codec<S>;
   using T = typename C::T;
   using L = Lat<QP>;
+  using YS = YSlots<QP>;
+  constexpr int NY = NYOf<QP>::value;
   const WorkItem it = items[blockIdx.x];
   const SimDev& sd = sims[it.sim];
   const int nx = sd.nx, ny = sd.ny, nz = sd.nz;
   const int BY = blockDim.y;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * 32 + tx, nthr = 32 * BY;
-  const int x = it.x0 - 1 + tx, y = it.y0 - 1 + ty;
-  const bool in_xy = x >= 0 && x < nx && y >= 0 && y < ny;
-  const bool icol = in_xy && tx >= 1 && tx <= TILE_X && ty >= 1 && ty <= BY - 2;
+  const int x = it.x0 - 1 + tx;
   const int par = s6 & 1;
-  const long long NS = sd.nsite;
+  // element offsets fit in 32 bits (Q * nsite < 2^32 is checked at create)
+  const unsigned NS = (unsigned)sd.nsite;
+  const unsigned plane = (unsigned)ny * (unsigned)nx;
   const S* __restrict__ gin = (const S*)sd.pop[par][0];
   S* __restrict__ gout = (S*)sd.pop[par ^ 1][0];
   const T* __restrict__ phin = (const T*)sd.phi[s6 % 3];
@@ -261,12 +354,11 @@ __global__ void __launch_bounds__(512) k_phi(const SimDev* __restrict__ sims, co
   const T* __restrict__ thn = (const T*)sd.th[par];
   const bool has_th = sd.q_theta != 0;
 
-  const int RW = 34, RH = BY + 2, RS = RW * RH;
+  const int RW = 34, RS = RW * (BY + 2), PS = BY * 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* ring = reinterpret_cast<T*>(smem_raw);        // phi^n     [3][RH][RW]
-  T* ringm = ring + 3 * RS;                        // phi^{n-1} [3][RH][RW] (codec shift only)
-  T* sG = ring + (C::shifted ? 6 : 3) * RS;        // post-collision [QP][BY][32]
-  const int PS = BY * 32;
+  T* ring = reinterpret_cast<T*>(smem_raw);  // phi^n     [4][BY+2][34]
+  T* ringm = ring + 4 * RS;                  // phi^{n-1} [4][BY+2][34] (codec shift only)
+  T* sG = ring + (C::shifted ? 8 : 4) * RS;  // [2][NY][BY][32]
 
   const T inv2dx = (T)sd.inv2dx, c_eta = (T)sd.c_eta, c_N = (T)sd.c_N, dt_tau0 = (T)sd.dt_tau0;
   const T lamM = (T)sd.lamM, lam = (T)sd.lam, e1 = (T)sd.eps1, e2 = (T)sd.eps2, g2min = (T)sd.grad2_min;
@@ -274,113 +366,229 @@ __global__ void __launch_bounds__(512) k_phi(const SimDev* __restrict__ sims, co
   const int kind = sd.aniso;
 
   const int zlo = max(it.z0 - 1, 0), zhi = min(it.z1, nz - 1);
-  load_ring(ring + ring_slot(zlo - 1) * RS, phin, zlo - 1, it.x0, it.y0, nx, ny, nz, RW, RS, tid, nthr);
-  load_ring(ring + ring_slot(zlo) * RS, phin, zlo, it.x0, it.y0, nx, ny, nz, RW, RS, tid, nthr);
-  if (C::shifted) {
-    load_ring(ringm + ring_slot(zlo - 1) * RS, phim, zlo - 1, it.x0, it.y0, nx, ny, nz, RW, RS, tid, nthr);
-    load_ring(ringm + ring_slot(zlo) * RS, phim, zlo, it.x0, it.y0, nx, ny, nz, RW, RS, tid, nthr);
+  RingMap rm;
+  rm.init(it.x0, it.y0, nx, ny, RW, RS, tid, nthr);
+  {
+    RingRegs<T> a;
+    for (int z = zlo - 1; z <= zlo + 1; ++z) {
+      a.fetch(rm, phin, z, nz, plane);
+      a.store(rm, ring + slot4(z) * RS, tid, nthr);
+      if (C::shifted) {
+        a.fetch(rm, phim, z, nz, plane);
+        a.store(rm, ringm + slot4(z) * RS, tid, nthr);
+      }
+    }
   }
-  T acc0 = 0, acc1 = 0, acc2 = 0;  // moments of planes zc-1, zc, zc+1
-  const int rc = (ty + 1) * RW + (tx + 1);  // this node's ring offset
+  RingRegs<T> pf, pfm;
+  if (zlo + 2 <= zhi + 1) {
+    pf.fetch(rm, phin, zlo + 2, nz, plane);
+    if (C::shifted) pfm.fetch(rm, phim, zlo + 2, nz, plane);
+  }
+  T a0A = 0, a1A = 0, a2A = 0;  // moments of planes zc-1, zc, zc+1
+  int buf = 0;
+  __syncthreads();
 
   for (int zc = zlo; zc <= zhi; ++zc) {
-    load_ring(ring + ring_slot(zc + 1) * RS, phin, zc + 1, it.x0, it.y0, nx, ny, nz, RW, RS, tid, nthr);
-    if (C::shifted)
-      load_ring(ringm + ring_slot(zc + 1) * RS, phim, zc + 1, it.x0, it.y0, nx, ny, nz, RW, RS, tid, nthr);
-    __syncthreads();
-    const T* R0 = ring + ring_slot(zc) * RS;
-    if (in_xy) {
-      const T* Rp = ring + ring_slot(zc + 1) * RS;
-      const T* Rm = ring + ring_slot(zc - 1) * RS;
-      const long long site = ((long long)zc * ny + y) * nx + x;
-      const T ph = R0[rc];
-      // centred gradient with mirror ghosts (clamped ring)
-      const T gx = (R0[rc + 1] - R0[rc - 1]) * inv2dx;
-      const T gy = (R0[rc + RW] - R0[rc - RW]) * inv2dx;
-      const T gz = (Rp[rc] - Rm[rc]) * inv2dx;
-      const T G2 = gx * gx + gy * gy + gz * gz;
-      T as = 1, Nx = 0, Ny = 0, Nz = 0;
-      if (G2 >= g2min) as = aniso_N<T>(kind, e1, e2, gx, gy, gz, G2, Nx, Ny, Nz);
-      const T as2 = as * as;
-      const T inv_eta = T(1) / (c_eta * as2 + T(0.5));
-      const T omp2 = T(1) - ph * ph;
-      const T th = has_th ? thn[site] : theta0;
-      const T Qdt = (ph - (lamM * Un[site] + lam * th) * omp2) * omp2 * dt_tau0;
+    T* sGb = sG + buf * NY * PS;
+    const T* R0 = ring + slot4(zc) * RS;
+    const T* Rp = ring + slot4(zc + 1) * RS;
+    const T* Rm = ring + slot4(zc - 1) * RS;
+    auto collide_row = [&](const int r, T& acc0, T& acc1, T& acc2) {
+      const int ly = ty;
+      const int y = it.y0 - 1 + ly;
+      const bool in_xy = x >= 0 && x < nx && y >= 0 && y < ny;
+      const bool icol = in_xy && tx >= 1 && tx <= TILE_X && ly >= 1 && ly <= BY - 2;
+      const int rc = (ly + 1) * RW + (tx + 1);
+      const unsigned site = ((unsigned)zc * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
       const bool bnd = x == 0 || y == 0 || zc == 0 || x == nx - 1 || y == ny - 1 || zc == nz - 1;
-      const T a2 = bnd ? T(1) : as2;
-      const T inv_a2 = T(1) / a2;
-      const T oma2 = T(1) - a2;
-      const bool store = icol && zc >= it.z0 && zc < it.z1;
-      const T* RmP = ringm + ring_slot(zc) * RS;
+      T gs[QP];
+#pragma unroll
+      for (int i = 0; i < QP; ++i) gs[i] = T(0);
+      if (in_xy) {
+        const T Usite = ldro(Un + site);
+        const T thsite = has_th ? ldro(thn + site) : theta0;
+        // pulled populations g_i(x,t) and non-local values g_i(x+e_i,t), all loads first
+        T gpull[QP], gnl[QP];
+        if (!bnd) {
+#pragma unroll
+          for (int i = 0; i < QP; ++i) {
+            const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
+            const T wi = (T)L::w(i);
+            const unsigned own = (unsigned)i * NS + site;
+            const unsigned off = (unsigned)(ez * (int)plane + ey * nx + ex);
+            T shift_in = 0, shift_nl = 0;
+            if (C::shifted) {
+              shift_in = wi * (ringm + slot4(zc - ez) * RS)[rc - ey * RW - ex];
+              shift_nl = wi * (ringm + slot4(zc) * RS)[rc];
+            }
+            gpull[i] = C::dec(ldro(gin + (own - off)), shift_in, iscale);
+            gnl[i] = C::dec(ldro(gin + own), shift_nl, iscale);
+          }
+        } else {
+          // wall node: bounce-back for links from outside, standard collision (no non-local term)
+#pragma unroll
+          for (int i = 0; i < QP; ++i) {
+            const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
+            const T wi = (T)L::w(i);
+            const int sx = x - ex, sy = y - ey, sz = zc - ez;
+            const bool inside = sx >= 0 && sx < nx && sy >= 0 && sy < ny && sz >= 0 && sz < nz;
+            const unsigned src = inside ? site - (unsigned)(ez * (int)plane + ey * nx + ex) : site;
+            const int ii = inside ? i : L::opp(i);
+            T shift_in = 0;
+            if (C::shifted) {
+              const T* Rs = ringm + slot4(inside ? sz : zc) * RS;
+              shift_in = wi * Rs[inside ? rc - ey * RW - ex : rc];
+            }
+            gpull[i] = C::dec(ldro(gin + ((unsigned)ii * NS + src)), shift_in, iscale);
+            gnl[i] = T(0);
+          }
+        }
+        const T ph = R0[rc];
+        // centred gradient with mirror ghosts (clamped ring)
+        const T gx = (R0[rc + 1] - R0[rc - 1]) * inv2dx;
+        const T gy = (R0[rc + RW] - R0[rc - RW]) * inv2dx;
+        const T gz = (Rp[rc] - Rm[rc]) * inv2dx;
+        const T G2 = gx * gx + gy * gy + gz * gz;
+        T as = 1, Nx = 0, Ny = 0, Nz = 0;
+        if (G2 >= g2min) as = aniso_N<T>(kind, e1, e2, gx, gy, gz, G2, Nx, Ny, Nz);
+        const T as2 = as * as;
+        const T inv_eta = rcp(c_eta * as2 + T(0.5));
+        const T omp2 = T(1) - ph * ph;
+        const T Qdt = (ph - (lamM * Usite + lam * thsite) * omp2) * omp2 * dt_tau0;
+        const T a2 = bnd ? T(1) : as2;
+        const T inv_a2 = bnd ? T(1) : rcp(a2);
+        const T oma2 = T(1) - a2;
+        const bool store = icol && zc >= it.z0 && zc < it.z1;
+#pragma unroll
+        for (int i = 0; i < QP; ++i) {
+          const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
+          const T wi = (T)L::w(i);
+          const T eN = (T)ex * Nx + (T)ey * Ny + (T)ez * Nz;
+          const T g0 = wi * (ph - eN * c_N);
+          const T g = (gpull[i] - oma2 * gnl[i] - (gpull[i] - g0) * inv_eta + wi * Qdt) * inv_a2;
+          const T shift_out = C::shifted ? wi * ph : T(0);
+          const auto enc = C::enc(g, shift_out, scale);
+          if (store) gout[(unsigned)i * NS + site] = enc;
+          gs[i] = C::shifted ? C::dec(enc, shift_out, iscale) : g;
+          if (ey != 0) sGb[YS::slot(i) * PS + ly * 32 + tx] = gs[i];
+        }
+      }
+      // populations with e_y = 0: from this lane or the x-neighbour lane (all lanes shuffle)
+      T sv[QP];
 #pragma unroll
       for (int i = 0; i < QP; ++i) {
-        const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
-        const T wi = (T)L::w(i);
-        const int sx = x - ex, sy = y - ey, sz = zc - ez;
-        const bool inside = sx >= 0 && sx < nx && sy >= 0 && sy < ny && sz >= 0 && sz < nz;
-        const long long src = inside ? site - ((long long)ez * ny + ey) * nx - ex : site;
-        const int ii = inside ? i : L::opp(i);
-        T shift_in = 0, shift_nl = 0;
-        if (C::shifted) {
-          const T* Rs = ringm + ring_slot(inside ? sz : zc) * RS;
-          shift_in = wi * Rs[inside ? rc - ey * RW - ex : rc];
-          shift_nl = wi * RmP[rc];
-        }
-        const T gpull = C::dec(gin[(long long)ii * NS + src], shift_in, iscale);
-        const T gnl = bnd ? T(0) : C::dec(gin[(long long)i * NS + site], shift_nl, iscale);
-        const T eN = (T)ex * Nx + (T)ey * Ny + (T)ez * Nz;
-        const T g0 = wi * (ph - eN * c_N);
-        const T gs = (gpull - oma2 * gnl - (gpull - g0) * inv_eta + wi * Qdt) * inv_a2;
-        const T shift_out = C::shifted ? wi * ph : T(0);
-        const auto enc = C::enc(gs, shift_out, scale);
-        if (store) gout[(long long)i * NS + site] = enc;
-        sG[i * PS + tid] = C::shifted ? C::dec(enc, shift_out, iscale) : gs;
+        const int ex = L::ex(i), ey = L::ey(i);
+        sv[i] = gs[i];
+        if (ey == 0 && ex > 0) sv[i] = __shfl_up_sync(0xffffffffu, gs[i], 1);
+        if (ey == 0 && ex < 0) sv[i] = __shfl_down_sync(0xffffffffu, gs[i], 1);
       }
+      if (icol) {
+        if (!bnd) {
+#pragma unroll
+          for (int i = 0; i < QP; ++i) {
+            const int ey = L::ey(i), ez = L::ez(i);
+            if (ey != 0) continue;
+            if (ez < 0) acc0 += sv[i];
+            else if (ez > 0) acc2 += sv[i];
+            else acc1 += sv[i];
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < QP; ++i) {
+            const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
+            if (ey != 0) continue;
+            const int sx = x - ex, sz = zc - ez;
+            const bool sin = sx >= 0 && sx < nx;
+            if (sin) {
+              if (ez < 0) acc0 += sv[i];
+              else if (ez > 0) acc2 += sv[i];
+              else acc1 += sv[i];
+            }
+            if (!sin || sz < 0 || sz >= nz) acc1 += gs[L::opp(i)];
+          }
+        }
+      }
+    };
+    collide_row(0, a0A, a1A, a2A);
+    // ring plane zc+2 (its slot last held plane zc-2), then prefetch zc+3
+    if (zc + 2 <= zhi + 1) {
+      pf.store(rm, ring + slot4(zc + 2) * RS, tid, nthr);
+      if (C::shifted) pfm.store(rm, ringm + slot4(zc + 2) * RS, tid, nthr);
+    }
+    if (zc + 3 <= zhi + 1) {
+      pf.fetch(rm, phin, zc + 3, nz, plane);
+      if (C::shifted) pfm.fetch(rm, phim, zc + 3, nz, plane);
     }
     __syncthreads();
-    if (icol) {
+    // populations with e_y != 0: from the neighbouring rows through shared memory
+    auto gather_row = [&](const int r, T& acc0, T& acc1, T& acc2) {
+      const int ly = ty;
+      const int y = it.y0 - 1 + ly;
+      const bool icol = x >= 0 && x < nx && y >= 0 && y < ny && tx >= 1 && tx <= TILE_X && ly >= 1 && ly <= BY - 2;
+      if (icol) {
+        const bool inner = x >= 1 && y >= 1 && zc >= 1 && x <= nx - 2 && y <= ny - 2 && zc <= nz - 2;
+        if (inner) {
 #pragma unroll
-      for (int i = 0; i < QP; ++i) {
-        const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
-        const int sx = x - ex, sy = y - ey, sz = zc - ez;
-        const bool sin_xy = sx >= 0 && sx < nx && sy >= 0 && sy < ny;
-        if (sin_xy) {
-          const T v = sG[i * PS + tid - ey * 32 - ex];
-          if (ez == 0) acc1 += v;
-          else if (ez > 0) acc2 += v;
-          else acc0 += v;
+          for (int i = 0; i < QP; ++i) {
+            const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
+            if (ey == 0) continue;
+            const T v = sGb[YS::slot(i) * PS + (ly - ey) * 32 + tx - ex];
+            if (ez < 0) acc0 += v;
+            else if (ez > 0) acc2 += v;
+            else acc1 += v;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < QP; ++i) {
+            const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
+            if (ey == 0) continue;
+            const int sx = x - ex, sy = y - ey, sz = zc - ez;
+            const bool sin = sx >= 0 && sx < nx && sy >= 0 && sy < ny;
+            if (sin) {
+              const T v = sGb[YS::slot(i) * PS + (ly - ey) * 32 + tx - ex];
+              if (ez < 0) acc0 += v;
+              else if (ez > 0) acc2 += v;
+              else acc1 += v;
+            }
+            if (!sin || sz < 0 || sz >= nz) acc1 += sGb[YS::slot(L::opp(i)) * PS + ly * 32 + tx];
+          }
         }
-        if (!sin_xy || sz < 0 || sz >= nz) acc1 += sG[L::opp(i) * PS + tid];
+        const int zw = zc - 1;
+        if (zw >= it.z0 && zw < it.z1 && zw >= 0) phinew[((unsigned)zw * ny + y) * (unsigned)nx + x] = acc0;
+        if (zc == nz - 1 && zc >= it.z0 && zc < it.z1) phinew[((unsigned)zc * ny + y) * (unsigned)nx + x] = acc1;
       }
-      const int zw = zc - 1;
-      if (zw >= it.z0 && zw < it.z1 && zw >= 0) phinew[((long long)zw * ny + y) * nx + x] = acc0;
-    }
-    acc0 = acc1;
-    acc1 = acc2;
-    acc2 = 0;
+      acc0 = acc1;
+      acc1 = acc2;
+      acc2 = 0;
+    };
+    gather_row(0, a0A, a1A, a2A);
+    buf ^= 1;
   }
-  if (icol && zhi == nz - 1 && zhi >= it.z0 && zhi < it.z1) phinew[((long long)zhi * ny + y) * nx + x] = acc0;
 }
 
 // ---------------------------------------------------------------- U and theta
 template <int QU, int QT, typename S>
 __global__ void __launch_bounds__(512) k_uth(const SimDev* __restrict__ sims, const WorkItem* __restrict__ items,
-                                             int s6) {
+                                                int s6) {
   using C = Codec<S>;
   using T = typename C::T;
   using LU = Lat<QU>;
   using LT = Lat<(QT > 0 ? QT : 7)>;
+  using YU = YSlots<QU>;
+  using YT = YSlots<(QT > 0 ? QT : 7)>;
+  constexpr int NYU = NYOf<QU>::value;
+  constexpr int NYT = NYOf<QT>::value;
+  constexpr int QTA = QT > 0 ? QT : 1;
   const WorkItem it = items[blockIdx.x];
   const SimDev& sd = sims[it.sim];
   const int nx = sd.nx, ny = sd.ny, nz = sd.nz;
   const int BY = blockDim.y;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * 32 + tx, nthr = 32 * BY;
-  const int x = it.x0 - 1 + tx, y = it.y0 - 1 + ty;
-  const bool in_xy = x >= 0 && x < nx && y >= 0 && y < ny;
-  const bool icol = in_xy && tx >= 1 && tx <= TILE_X && ty >= 1 && ty <= BY - 2;
+  const int x = it.x0 - 1 + tx;
   const int par = s6 & 1;
-  const long long NS = sd.nsite;
+  const unsigned NS = (unsigned)sd.nsite;
+  const unsigned plane = (unsigned)ny * (unsigned)nx;
   const S* __restrict__ hin = (const S*)sd.pop[par][1];
   S* __restrict__ hout = (S*)sd.pop[par ^ 1][1];
   const S* __restrict__ fin = (const S*)sd.pop[par][2];
@@ -392,12 +600,11 @@ __global__ void __launch_bounds__(512) k_uth(const SimDev* __restrict__ sims, co
   const T* __restrict__ thn = (const T*)sd.th[par];
   T* __restrict__ thnew = (T*)sd.th[par ^ 1];
 
-  const int RW = 34, RH = BY + 2, RS = RW * RH;
+  const int RW = 34, RS = RW * (BY + 2), PS = BY * 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* ring = reinterpret_cast<T*>(smem_raw);  // phi^{n+1} [3][RH][RW]
-  T* sH = ring + 3 * RS;                     // [QU][BY][32]
-  const int PS = BY * 32;
-  T* sF = sH + QU * PS;                      // [QT][BY][32]
+  T* ring = reinterpret_cast<T*>(smem_raw);  // phi^{n+1} [4][BY+2][34]
+  T* sH = ring + 4 * RS;                     // [2][NYU + NYT][BY][32]
+  constexpr int NYA = NYU + NYT;
 
   const T inv2dx = (T)sd.inv2dx, k = (T)sd.k, inv_etaU = (T)sd.inv_etaU, c_J = (T)sd.c_J;
   const T D_dx2 = (T)sd.D_dx2, D = (T)sd.D, at_amp = (T)sd.at_amp, inv_dt = (T)sd.inv_dt, dt = (T)sd.dt;
@@ -408,139 +615,306 @@ __global__ void __launch_bounds__(512) k_uth(const SimDev* __restrict__ sims, co
   const T opk = T(1) + k, omk = T(1) - k;
 
   const int zlo = max(it.z0 - 1, 0), zhi = min(it.z1, nz - 1);
-  load_ring(ring + ring_slot(zlo - 1) * RS, phi1, zlo - 1, it.x0, it.y0, nx, ny, nz, RW, RS, tid, nthr);
-  load_ring(ring + ring_slot(zlo) * RS, phi1, zlo, it.x0, it.y0, nx, ny, nz, RW, RS, tid, nthr);
-  T u0 = 0, u1 = 0, u2 = 0, t0 = 0, t1 = 0, t2 = 0;
-  const int rc = (ty + 1) * RW + (tx + 1);
+  RingMap rm;
+  rm.init(it.x0, it.y0, nx, ny, RW, RS, tid, nthr);
+  {
+    RingRegs<T> a;
+    for (int z = zlo - 1; z <= zlo + 1; ++z) {
+      a.fetch(rm, phi1, z, nz, plane);
+      a.store(rm, ring + slot4(z) * RS, tid, nthr);
+    }
+  }
+  RingRegs<T> pf;
+  if (zlo + 2 <= zhi + 1) pf.fetch(rm, phi1, zlo + 2, nz, plane);
+  T u0A = 0, u1A = 0, u2A = 0, t0A = 0, t1A = 0, t2A = 0;
+  int buf = 0;
+  __syncthreads();
 
   for (int zc = zlo; zc <= zhi; ++zc) {
-    load_ring(ring + ring_slot(zc + 1) * RS, phi1, zc + 1, it.x0, it.y0, nx, ny, nz, RW, RS, tid, nthr);
-    __syncthreads();
-    if (in_xy) {
-      const T* R0 = ring + ring_slot(zc) * RS;
-      const T* Rp = ring + ring_slot(zc + 1) * RS;
-      const T* Rm = ring + ring_slot(zc - 1) * RS;
-      const long long site = ((long long)zc * ny + y) * nx + x;
-      // phi^{n+1} at the node and its six neighbours (mirror ghosts)
-      const T pc = R0[rc];
-      const T pxp = R0[rc + 1], pxm = R0[rc - 1], pyp = R0[rc + RW], pym = R0[rc - RW], pzp = Rp[rc], pzm = Rm[rc];
-      // q(phi) = (1 - phi)/2, zeta(phi) = ((1+k) - (1-k) phi)/2
-      auto qf = [&](T p) { return T(0.5) * (T(1) - p); };
-      auto izf = [&](T p) { return T(2) / (opk - omk * p); };
-      const T qc = qf(pc), izc = izf(pc), qzc = qc * izc;
-      const T iz_xp = izf(pxp), iz_xm = izf(pxm), iz_yp = izf(pyp), iz_ym = izf(pym), iz_zp = izf(pzp),
-              iz_zm = izf(pzm);
-      const T gpx = (pxp - pxm) * inv2dx, gpy = (pyp - pym) * inv2dx, gpz = (pzp - pzm) * inv2dx;
-      const T Fx = (iz_xp - iz_xm) * inv2dx, Fy = (iz_yp - iz_ym) * inv2dx, Fz = (iz_zp - iz_zm) * inv2dx;
-      const T gqzx = (qf(pxp) * iz_xp - qf(pxm) * iz_xm) * inv2dx;
-      const T gqzy = (qf(pyp) * iz_yp - qf(pym) * iz_ym) * inv2dx;
-      const T gqzz = (qf(pzp) * iz_zp - qf(pzm) * iz_zm) * inv2dx;
-      // div(D q grad(1/zeta)) in compact face form, face q = mean of nodal q
-      const T divDqF = D_dx2 * (T(0.5) * (qc + qf(pxp)) * (iz_xp - izc) - T(0.5) * (qc + qf(pxm)) * (izc - iz_xm) +
-                                T(0.5) * (qc + qf(pyp)) * (iz_yp - izc) - T(0.5) * (qc + qf(pym)) * (izc - iz_ym) +
-                                T(0.5) * (qc + qf(pzp)) * (iz_zp - izc) - T(0.5) * (qc + qf(pzm)) * (izc - iz_zm));
-      const T U = Un[site];
-      const T dphi = pc - phin[site];  // phi^{n+1} - phi^n
-      const T dphidt = dphi * inv_dt;
-      const T fU = T(1) + omk * U;
-      T jx = 0, jy = 0, jz = 0;
-      const T G2 = gpx * gpx + gpy * gpy + gpz * gpz;
-      if (at_on && G2 >= g2min) {
-        const T iG = (sizeof(T) == 8) ? T(1) / sqrt(G2) : rsqrtf((float)G2);
-        const T amp = -at_amp * fU * dphidt * iG;
-        jx = amp * gpx;
-        jy = amp * gpy;
-        jz = amp * gpz;
-      }
-      const T DqU = D * U;
-      const T Jx = DqU * (gqzx + qc * Fx) + jx * izc;
-      const T Jy = DqU * (gqzy + qc * Fy) + jy * izc;
-      const T Jz = DqU * (gqzz + qc * Fz) + jz * izc;
-      const T Ssrc = U * divDqF + (jx * Fx + jy * Fy + jz * Fz);
-      const T src_dt = (Ssrc + fU * T(0.5) * dphidt * izc) * dt;
-      const T qzU = qzc * U;
-      const bool store = icol && zc >= it.z0 && zc < it.z1;
+    T* sHb = sH + buf * NYA * PS;
+    T* sFb = sHb + NYU * PS;
+    const T* R0 = ring + slot4(zc) * RS;
+    const T* Rp = ring + slot4(zc + 1) * RS;
+    const T* Rm = ring + slot4(zc - 1) * RS;
+    auto collide_row = [&](const int r, T& u0, T& u1, T& u2, T& t0, T& t1, T& t2) {
+      const int ly = ty;
+      const int y = it.y0 - 1 + ly;
+      const bool in_xy = x >= 0 && x < nx && y >= 0 && y < ny;
+      const bool icol = in_xy && tx >= 1 && tx <= TILE_X && ly >= 1 && ly <= BY - 2;
+      const int rc = (ly + 1) * RW + (tx + 1);
+      const unsigned site = ((unsigned)zc * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
+      const bool inner = x >= 1 && y >= 1 && zc >= 1 && x <= nx - 2 && y <= ny - 2 && zc <= nz - 2;
+      T hs[QU], fs[QTA];
 #pragma unroll
-      for (int i = 0; i < QU; ++i) {
-        const int ex = LU::ex(i), ey = LU::ey(i), ez = LU::ez(i);
-        const T wi = (T)LU::w(i);
-        const int sx = x - ex, sy = y - ey, sz = zc - ez;
-        const bool inside = sx >= 0 && sx < nx && sy >= 0 && sy < ny && sz >= 0 && sz < nz;
-        const long long src = inside ? site - ((long long)ez * ny + ey) * nx - ex : site;
-        const int ii = inside ? i : LU::opp(i);
-        const T sh = C::shifted ? wi * sh_h : T(0);
-        const T hp = C::dec(hin[(long long)ii * NS + src], sh, isc_h);
-        const T eJ = (T)ex * Jx + (T)ey * Jy + (T)ez * Jz;
-        const T h0 = (i == 0 ? U : T(0)) + (T)LU::B(i) * (qzU + eJ * c_J);
-        const T hs = hp - (hp - h0) * inv_etaU + wi * src_dt;
-        const auto enc = C::enc(hs, sh, sc_h);
-        if (store) hout[(long long)i * NS + site] = enc;
-        sH[i * PS + tid] = C::shifted ? C::dec(enc, sh, isc_h) : hs;
-      }
-      if (QT > 0) {
-        const T th = thn[site];
-        const T qth_dt = T(0.5) * dphi;  // w_i Q_theta dt with Q_theta = dphi/dt / 2
+      for (int i = 0; i < QU; ++i) hs[i] = T(0);
 #pragma unroll
-        for (int i = 0; i < QT; ++i) {
-          const int ex = LT::ex(i), ey = LT::ey(i), ez = LT::ez(i);
-          const T wi = (T)LT::w(i);
-          const int sx = x - ex, sy = y - ey, sz = zc - ez;
-          const bool inside = sx >= 0 && sx < nx && sy >= 0 && sy < ny && sz >= 0 && sz < nz;
-          const long long src = inside ? site - ((long long)ez * ny + ey) * nx - ex : site;
-          const int ii = inside ? i : LT::opp(i);
-          const T sh = C::shifted ? wi * sh_f : T(0);
-          const T fp = C::dec(fin[(long long)ii * NS + src], sh, isc_f);
-          const T fs = fp - (fp - wi * th) * inv_etaT + wi * qth_dt;
-          const auto enc = C::enc(fs, sh, sc_f);
-          if (store) fout[(long long)i * NS + site] = enc;
-          sF[i * PS + tid] = C::shifted ? C::dec(enc, sh, isc_f) : fs;
-        }
-      }
-    }
-    __syncthreads();
-    if (icol) {
+      for (int i = 0; i < QTA; ++i) fs[i] = T(0);
+      if (in_xy) {
+        const T U = ldro(Un + site);
+        const T phn = ldro(phin + site);
+        const T th = QT > 0 ? ldro(thn + site) : T(0);
+        // pulled populations, all loads first; interior nodes need no wall checks
+        if (inner) {
 #pragma unroll
-      for (int i = 0; i < QU; ++i) {
-        const int ex = LU::ex(i), ey = LU::ey(i), ez = LU::ez(i);
-        const int sx = x - ex, sy = y - ey, sz = zc - ez;
-        const bool sin_xy = sx >= 0 && sx < nx && sy >= 0 && sy < ny;
-        if (sin_xy) {
-          const T v = sH[i * PS + tid - ey * 32 - ex];
-          if (ez == 0) u1 += v;
-          else if (ez > 0) u2 += v;
-          else u0 += v;
-        }
-        if (!sin_xy || sz < 0 || sz >= nz) u1 += sH[LU::opp(i) * PS + tid];
-      }
-      if (QT > 0) {
-#pragma unroll
-        for (int i = 0; i < QT; ++i) {
-          const int ex = LT::ex(i), ey = LT::ey(i), ez = LT::ez(i);
-          const int sx = x - ex, sy = y - ey, sz = zc - ez;
-          const bool sin_xy = sx >= 0 && sx < nx && sy >= 0 && sy < ny;
-          if (sin_xy) {
-            const T v = sF[i * PS + tid - ey * 32 - ex];
-            if (ez == 0) t1 += v;
-            else if (ez > 0) t2 += v;
-            else t0 += v;
+          for (int i = 0; i < QU; ++i) {
+            const int ex = LU::ex(i), ey = LU::ey(i), ez = LU::ez(i);
+            const T sh = C::shifted ? (T)LU::w(i) * sh_h : T(0);
+            hs[i] = C::dec(ldro(hin + ((unsigned)i * NS + site - (unsigned)(ez * (int)plane + ey * nx + ex))), sh, isc_h);
           }
-          if (!sin_xy || sz < 0 || sz >= nz) t1 += sF[LT::opp(i) * PS + tid];
+#pragma unroll
+          for (int i = 0; i < QT; ++i) {
+            const int ex = LT::ex(i), ey = LT::ey(i), ez = LT::ez(i);
+            const T sh = C::shifted ? (T)LT::w(i) * sh_f : T(0);
+            fs[i] = C::dec(ldro(fin + ((unsigned)i * NS + site - (unsigned)(ez * (int)plane + ey * nx + ex))), sh, isc_f);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < QU; ++i) {
+            const int ex = LU::ex(i), ey = LU::ey(i), ez = LU::ez(i);
+            const int sx = x - ex, sy = y - ey, sz = zc - ez;
+            const bool inside = sx >= 0 && sx < nx && sy >= 0 && sy < ny && sz >= 0 && sz < nz;
+            const unsigned src = inside ? site - (unsigned)(ez * (int)plane + ey * nx + ex) : site;
+            const int ii = inside ? i : LU::opp(i);
+            const T sh = C::shifted ? (T)LU::w(i) * sh_h : T(0);
+            hs[i] = C::dec(ldro(hin + ((unsigned)ii * NS + src)), sh, isc_h);
+          }
+#pragma unroll
+          for (int i = 0; i < QT; ++i) {
+            const int ex = LT::ex(i), ey = LT::ey(i), ez = LT::ez(i);
+            const int sx = x - ex, sy = y - ey, sz = zc - ez;
+            const bool inside = sx >= 0 && sx < nx && sy >= 0 && sy < ny && sz >= 0 && sz < nz;
+            const unsigned src = inside ? site - (unsigned)(ez * (int)plane + ey * nx + ex) : site;
+            const int ii = inside ? i : LT::opp(i);
+            const T sh = C::shifted ? (T)LT::w(i) * sh_f : T(0);
+            fs[i] = C::dec(ldro(fin + ((unsigned)ii * NS + src)), sh, isc_f);
+          }
+        }
+        // phi^{n+1} at the node and its six neighbours (mirror ghosts)
+        const T pc = R0[rc];
+        const T pxp = R0[rc + 1], pxm = R0[rc - 1], pyp = R0[rc + RW], pym = R0[rc - RW], pzp = Rp[rc], pzm = Rm[rc];
+        // q(phi) = (1 - phi)/2, zeta(phi) = ((1+k) - (1-k) phi)/2
+        auto qf = [&](T p) { return T(0.5) * (T(1) - p); };
+        // 1/zeta at the node and its six neighbours with one division (batch inversion):
+        // 2 zeta = (1+k) - (1-k) phi
+        const T d0 = opk - omk * pc, d1 = opk - omk * pxp, d2 = opk - omk * pxm, d3 = opk - omk * pyp,
+                d4 = opk - omk * pym, d5 = opk - omk * pzp, d6 = opk - omk * pzm;
+        const T p1 = d0 * d1, p2 = p1 * d2, p3 = p2 * d3, p4 = p3 * d4, p5 = p4 * d5, p6 = p5 * d6;
+        T rr = T(2) * rcp(p6);  // 2 / (d0 ... d6)
+        const T iz_zm = rr * p5;
+        rr *= d6;
+        const T iz_zp = rr * p4;
+        rr *= d5;
+        const T iz_ym = rr * p3;
+        rr *= d4;
+        const T iz_yp = rr * p2;
+        rr *= d3;
+        const T iz_xm = rr * p1;
+        rr *= d2;
+        const T iz_xp = rr * d0;
+        const T izc = rr * d1;
+        const T qc = qf(pc), qzc = qc * izc;
+        const T gpx = (pxp - pxm) * inv2dx, gpy = (pyp - pym) * inv2dx, gpz = (pzp - pzm) * inv2dx;
+        const T Fx = (iz_xp - iz_xm) * inv2dx, Fy = (iz_yp - iz_ym) * inv2dx, Fz = (iz_zp - iz_zm) * inv2dx;
+        const T gqzx = (qf(pxp) * iz_xp - qf(pxm) * iz_xm) * inv2dx;
+        const T gqzy = (qf(pyp) * iz_yp - qf(pym) * iz_ym) * inv2dx;
+        const T gqzz = (qf(pzp) * iz_zp - qf(pzm) * iz_zm) * inv2dx;
+        // div(D q grad(1/zeta)) in compact face form, face q = mean of nodal q
+        const T divDqF =
+            D_dx2 * (T(0.5) * (qc + qf(pxp)) * (iz_xp - izc) - T(0.5) * (qc + qf(pxm)) * (izc - iz_xm) +
+                     T(0.5) * (qc + qf(pyp)) * (iz_yp - izc) - T(0.5) * (qc + qf(pym)) * (izc - iz_ym) +
+                     T(0.5) * (qc + qf(pzp)) * (iz_zp - izc) - T(0.5) * (qc + qf(pzm)) * (izc - iz_zm));
+        const T dphi = pc - phn;  // phi^{n+1} - phi^n
+        const T dphidt = dphi * inv_dt;
+        const T fU = T(1) + omk * U;
+        T jx = 0, jy = 0, jz = 0;
+        const T G2 = gpx * gpx + gpy * gpy + gpz * gpz;
+        if (at_on && G2 >= g2min) {
+          const T iG = (sizeof(T) == 8) ? T(1) / sqrt(G2) : rsqrtf((float)G2);
+          const T amp = -at_amp * fU * dphidt * iG;
+          jx = amp * gpx;
+          jy = amp * gpy;
+          jz = amp * gpz;
+        }
+        const T DqU = D * U;
+        const T Jx = DqU * (gqzx + qc * Fx) + jx * izc;
+        const T Jy = DqU * (gqzy + qc * Fy) + jy * izc;
+        const T Jz = DqU * (gqzz + qc * Fz) + jz * izc;
+        const T Ssrc = U * divDqF + (jx * Fx + jy * Fy + jz * Fz);
+        const T src_dt = (Ssrc + fU * T(0.5) * dphidt * izc) * dt;
+        const T qzU = qzc * U;
+        const bool store = icol && zc >= it.z0 && zc < it.z1;
+#pragma unroll
+        for (int i = 0; i < QU; ++i) {
+          const int ex = LU::ex(i), ey = LU::ey(i), ez = LU::ez(i);
+          const T wi = (T)LU::w(i);
+          const T sh = C::shifted ? wi * sh_h : T(0);
+          const T eJ = (T)ex * Jx + (T)ey * Jy + (T)ez * Jz;
+          const T h0 = (i == 0 ? U : T(0)) + (T)LU::B(i) * (qzU + eJ * c_J);
+          const T h = hs[i] - (hs[i] - h0) * inv_etaU + wi * src_dt;
+          const auto enc = C::enc(h, sh, sc_h);
+          if (store) hout[(unsigned)i * NS + site] = enc;
+          hs[i] = C::shifted ? C::dec(enc, sh, isc_h) : h;
+          if (ey != 0) sHb[YU::slot(i) * PS + ly * 32 + tx] = hs[i];
+        }
+        if (QT > 0) {
+          const T qth_dt = T(0.5) * dphi;  // w_i Q_theta dt with Q_theta = dphi/dt / 2
+#pragma unroll
+          for (int i = 0; i < QT; ++i) {
+            const int ey = LT::ey(i);
+            const T wi = (T)LT::w(i);
+            const T sh = C::shifted ? wi * sh_f : T(0);
+            const T f = fs[i] - (fs[i] - wi * th) * inv_etaT + wi * qth_dt;
+            const auto enc = C::enc(f, sh, sc_f);
+            if (store) fout[(unsigned)i * NS + site] = enc;
+            fs[i] = C::shifted ? C::dec(enc, sh, isc_f) : f;
+            if (ey != 0) sFb[YT::slot(i) * PS + ly * 32 + tx] = fs[i];
+          }
         }
       }
-      const int zw = zc - 1;
-      if (zw >= it.z0 && zw < it.z1 && zw >= 0) {
-        const long long sw = ((long long)zw * ny + y) * nx + x;
-        Unew[sw] = u0;
-        if (QT > 0) thnew[sw] = t0;
+      // populations with e_y = 0: from this lane or the x-neighbour lane (all lanes shuffle)
+      T hv[QU], fv[QTA];
+#pragma unroll
+      for (int i = 0; i < QU; ++i) {
+        const int ex = LU::ex(i), ey = LU::ey(i);
+        hv[i] = hs[i];
+        if (ey == 0 && ex > 0) hv[i] = __shfl_up_sync(0xffffffffu, hs[i], 1);
+        if (ey == 0 && ex < 0) hv[i] = __shfl_down_sync(0xffffffffu, hs[i], 1);
       }
-    }
-    u0 = u1; u1 = u2; u2 = 0;
-    t0 = t1; t1 = t2; t2 = 0;
-  }
-  if (icol && zhi == nz - 1 && zhi >= it.z0 && zhi < it.z1) {
-    const long long sw = ((long long)zhi * ny + y) * nx + x;
-    Unew[sw] = u0;
-    if (QT > 0) thnew[sw] = t0;
+#pragma unroll
+      for (int i = 0; i < QT; ++i) {
+        const int ex = LT::ex(i), ey = LT::ey(i);
+        fv[i] = fs[i];
+        if (ey == 0 && ex > 0) fv[i] = __shfl_up_sync(0xffffffffu, fs[i], 1);
+        if (ey == 0 && ex < 0) fv[i] = __shfl_down_sync(0xffffffffu, fs[i], 1);
+      }
+      if (icol) {
+        if (inner) {
+#pragma unroll
+          for (int i = 0; i < QU; ++i) {
+            const int ey = LU::ey(i), ez = LU::ez(i);
+            if (ey != 0) continue;
+            if (ez < 0) u0 += hv[i];
+            else if (ez > 0) u2 += hv[i];
+            else u1 += hv[i];
+          }
+#pragma unroll
+          for (int i = 0; i < QT; ++i) {
+            const int ey = LT::ey(i), ez = LT::ez(i);
+            if (ey != 0) continue;
+            if (ez < 0) t0 += fv[i];
+            else if (ez > 0) t2 += fv[i];
+            else t1 += fv[i];
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < QU; ++i) {
+            const int ex = LU::ex(i), ey = LU::ey(i), ez = LU::ez(i);
+            if (ey != 0) continue;
+            const int sx = x - ex, sz = zc - ez;
+            const bool sin = sx >= 0 && sx < nx;
+            if (sin) {
+              if (ez < 0) u0 += hv[i];
+              else if (ez > 0) u2 += hv[i];
+              else u1 += hv[i];
+            }
+            if (!sin || sz < 0 || sz >= nz) u1 += hs[LU::opp(i)];
+          }
+#pragma unroll
+          for (int i = 0; i < QT; ++i) {
+            const int ex = LT::ex(i), ey = LT::ey(i), ez = LT::ez(i);
+            if (ey != 0) continue;
+            const int sx = x - ex, sz = zc - ez;
+            const bool sin = sx >= 0 && sx < nx;
+            if (sin) {
+              if (ez < 0) t0 += fv[i];
+              else if (ez > 0) t2 += fv[i];
+              else t1 += fv[i];
+            }
+            if (!sin || sz < 0 || sz >= nz) t1 += fs[LT::opp(i)];
+          }
+        }
+      }
+    };
+    collide_row(0, u0A, u1A, u2A, t0A, t1A, t2A);
+    if (zc + 2 <= zhi + 1) pf.store(rm, ring + slot4(zc + 2) * RS, tid, nthr);
+    if (zc + 3 <= zhi + 1) pf.fetch(rm, phi1, zc + 3, nz, plane);
+    __syncthreads();
+    auto gather_row = [&](const int r, T& u0, T& u1, T& u2, T& t0, T& t1, T& t2) {
+      const int ly = ty;
+      const int y = it.y0 - 1 + ly;
+      const bool icol = x >= 0 && x < nx && y >= 0 && y < ny && tx >= 1 && tx <= TILE_X && ly >= 1 && ly <= BY - 2;
+      if (icol) {
+        const bool inner = x >= 1 && y >= 1 && zc >= 1 && x <= nx - 2 && y <= ny - 2 && zc <= nz - 2;
+        if (inner) {
+#pragma unroll
+          for (int i = 0; i < QU; ++i) {
+            const int ex = LU::ex(i), ey = LU::ey(i), ez = LU::ez(i);
+            if (ey == 0) continue;
+            const T v = sHb[YU::slot(i) * PS + (ly - ey) * 32 + tx - ex];
+            if (ez < 0) u0 += v;
+            else if (ez > 0) u2 += v;
+            else u1 += v;
+          }
+#pragma unroll
+          for (int i = 0; i < QT; ++i) {
+            const int ex = LT::ex(i), ey = LT::ey(i), ez = LT::ez(i);
+            if (ey == 0) continue;
+            const T v = sFb[YT::slot(i) * PS + (ly - ey) * 32 + tx - ex];
+            if (ez < 0) t0 += v;
+            else if (ez > 0) t2 += v;
+            else t1 += v;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < QU; ++i) {
+            const int ex = LU::ex(i), ey = LU::ey(i), ez = LU::ez(i);
+            if (ey == 0) continue;
+            const int sx = x - ex, sy = y - ey, sz = zc - ez;
+            const bool sin = sx >= 0 && sx < nx && sy >= 0 && sy < ny;
+            if (sin) {
+              const T v = sHb[YU::slot(i) * PS + (ly - ey) * 32 + tx - ex];
+              if (ez < 0) u0 += v;
+              else if (ez > 0) u2 += v;
+              else u1 += v;
+            }
+            if (!sin || sz < 0 || sz >= nz) u1 += sHb[YU::slot(LU::opp(i)) * PS + ly * 32 + tx];
+          }
+#pragma unroll
+          for (int i = 0; i < QT; ++i) {
+            const int ex = LT::ex(i), ey = LT::ey(i), ez = LT::ez(i);
+            if (ey == 0) continue;
+            const int sx = x - ex, sy = y - ey, sz = zc - ez;
+            const bool sin = sx >= 0 && sx < nx && sy >= 0 && sy < ny;
+            if (sin) {
+              const T v = sFb[YT::slot(i) * PS + (ly - ey) * 32 + tx - ex];
+              if (ez < 0) t0 += v;
+              else if (ez > 0) t2 += v;
+              else t1 += v;
+            }
+            if (!sin || sz < 0 || sz >= nz) t1 += sFb[YT::slot(LT::opp(i)) * PS + ly * 32 + tx];
+          }
+        }
+        const int zw = zc - 1;
+        if (zw >= it.z0 && zw < it.z1 && zw >= 0) {
+          const unsigned sw = ((unsigned)zw * ny + y) * (unsigned)nx + x;
+          Unew[sw] = u0;
+          if (QT > 0) thnew[sw] = t0;
+        }
+        if (zc == nz - 1 && zc >= it.z0 && zc < it.z1) {
+          const unsigned sw = ((unsigned)zc * ny + y) * (unsigned)nx + x;
+          Unew[sw] = u1;
+          if (QT > 0) thnew[sw] = t1;
+        }
+      }
+      u0 = u1;
+      u1 = u2;
+      u2 = 0;
+      t0 = t1;
+      t1 = t2;
+      t2 = 0;
+    };
+    gather_row(0, u0A, u1A, u2A, t0A, t1A, t2A);
+    buf ^= 1;
   }
 }
 

@@ -40,14 +40,18 @@ const KernelTable& table_f32();
 const KernelTable& table_f16();
 const KernelTable& table_bf16();
 
-// shared-memory bytes of the step kernels for a block of 32 x by threads
+// populations with e_y != 0 (they cross block rows in the moment gather)
+inline int ny_count(int q) { return q == 7 ? 2 : (q == 15 ? 10 : (q == 19 ? 10 : 0)); }
+
+// shared-memory bytes of the step kernels for a block of 32 x by threads: four ring planes of (by+2) x 34 scalars (eight with the
+// FP16/BF16 codec in k_phi) and a double-buffered plane of the e_y != 0 populations
 inline size_t phi_smem_bytes(const KernelTable& t, int qp, int by) {
   const size_t rs = 34u * (size_t)(by + 2);
-  return ((t.shifted ? 6 : 3) * rs + (size_t)qp * 32u * by) * t.tbytes;
+  return ((t.shifted ? 8 : 4) * rs + 2 * (size_t)ny_count(qp) * 32u * by) * t.tbytes;
 }
 inline size_t uth_smem_bytes(const KernelTable& t, int qu, int qt, int by) {
   const size_t rs = 34u * (size_t)(by + 2);
-  return (3 * rs + (size_t)(qu + qt) * 32u * by) * t.tbytes;
+  return (4 * rs + 2 * (size_t)(ny_count(qu) + ny_count(qt)) * 32u * by) * t.tbytes;
 }
 
 }  // namespace lbpf

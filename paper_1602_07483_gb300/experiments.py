@@ -1,0 +1,155 @@
+"""Runs of the workloads that report accuracy and throughput per precision.
+
+    python -m paper_1602_07483_gb300.experiments precision   # 256^3 coupled run, FP64/FP32/FP16
+    python -m paper_1602_07483_gb300.experiments dendrite    # 128^3, tip every 100 steps, D3Q19 and D3Q7 phi
+    python -m paper_1602_07483_gb300.experiments sweep       # 64 uneven simulations, batched FP16 vs one-by-one FP64
+
+Every number comes from the CUDA library through its C ABI; each run prints one
+JSON object.  FP32/FP16 errors are measured against the FP64 GPU path, which the
+test-suite pins to the CPU oracle step by step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import sys
+import time
+
+import numpy as np
+
+from . import build, lbpf, workloads
+
+
+def _sync():
+    try:
+        import torch
+        torch.cuda.synchronize()
+    except Exception:
+        pass
+
+
+def _tip_series(sim, centre, steps, every):
+    xs = []
+    done = 0
+    while done < steps:
+        k = min(every, steps - done)
+        sim.step(k)
+        done += k
+        x, rho = sim.tip(centre)
+        xs.append((done, x, rho))
+    return xs
+
+
+def _velocity(series, dx, dt, last_steps):
+    """Mean tip speed (physical units) over the last `last_steps` steps of a tip series."""
+    end = series[-1]
+    start = min(series, key=lambda r: abs((end[0] - r[0]) - last_steps))
+    if start[1] < 0 or end[1] < 0 or end[0] == start[0]:
+        return None
+    return (end[1] - start[1]) * dx / ((end[0] - start[0]) * dt)
+
+
+def precision(n=256, steps=8000, every=100, linf_at=200, storages=("f64", "f32", "f16", "bf16")):
+    w = workloads.coupled_dendrite(n=n)
+    c = [int(v) for v in w.centres[0]]
+    out = {"workload": w.name.replace("_f64", ""), "grid": n, "steps": steps, "dt": w.params["dt"], "runs": {}}
+    ref_fields = None
+    ref_v = None
+    for st in storages:
+        s = lbpf.sim_from_workload(w, storage=st)
+        s.step(linf_at)
+        f200 = s.read_fields()
+        _sync()
+        t0 = time.perf_counter()
+        series = _tip_series(s, c, steps - linf_at, every)
+        _sync()
+        el = time.perf_counter() - t0
+        v = _velocity(series, w.params["dx"], w.params["dt"], 2000)
+        r = {"GLUPS_incl_diagnostics": w.sites * (steps - linf_at) / el / 1e9,
+             "tip_velocity": v, "tip_x_final": series[-1][1], "tip_radius_final": series[-1][2],
+             "sums_final": s.sums(check=False).tolist()}
+        if st == "f64":
+            ref_fields, ref_v, ref_rho = f200, v, series[-1][2]
+        else:
+            r["phi_linf_at_%d" % linf_at] = float(np.abs(f200[0] - ref_fields[0]).max())
+            r["U_linf_at_%d" % linf_at] = float(np.abs(f200[1] - ref_fields[1]).max())
+            r["theta_linf_at_%d" % linf_at] = float(np.abs(f200[2] - ref_fields[2]).max())
+            if v is not None and ref_v:
+                r["tip_velocity_rel_err"] = v / ref_v - 1
+            if ref_rho and ref_rho > 0 and series[-1][2] > 0:
+                r["tip_radius_rel_err"] = series[-1][2] / ref_rho - 1
+        out["runs"][st] = r
+        s.close()
+        print(json.dumps({st: r}), file=sys.stderr, flush=True)
+    return out
+
+
+def dendrite(n=128, steps=5000, every=100):
+    out = {"grid": n, "steps": steps, "runs": {}}
+    for qphi in (19, 7):
+        w = workloads.single_dendrite(q_phi=qphi).with_(grid=(n, n, n))
+        c = [int(v) for v in w.centres[0]]
+        s = lbpf.sim_from_workload(w, storage="f64")
+        series = _tip_series(s, c, steps, every)
+        # the seed also grows along -x and along y: report the tips along the three axes
+        out["runs"]["phi_D3Q%d" % qphi] = {
+            "tip_series": [(k, round(x, 4), round(r, 4)) for k, x, r in series],
+            "tip_velocity_last_2000": _velocity(series, w.params["dx"], w.params["dt"], 2000),
+            "d0": 5 * np.sqrt(2) / 8 / w.params["lam"],
+        }
+        s.close()
+    return out
+
+
+def sweep(count=64, steps=2000, baseline_steps=200):
+    sims = workloads.batch_sweep(count=count, storage="f16")
+    sites = sum(w.sites for w in sims)
+    members = [lbpf.sim_from_workload(w) for w in sims]
+    batch = lbpf.Batch(members)
+    batch.step(6)
+    _sync()
+    members[0].sums(check=False)
+    t0 = time.perf_counter()
+    batch.step(steps)
+    members[0].sums(check=False)
+    _sync()
+    el = time.perf_counter() - t0
+    nan = [i for i, m in enumerate(members) if not np.all(np.isfinite(m.sums(check=False)))]
+    batch.close()
+    for m in members:
+        m.close()
+    # one-by-one plain FP64 on the same simulations (fewer steps; a rate)
+    t_one = 0.0
+    for w in sims:
+        s = lbpf.sim_from_workload(w, storage="f64")
+        s.step(6)
+        s.sums(check=False)
+        t0 = time.perf_counter()
+        s.step(baseline_steps)
+        s.sums(check=False)
+        t_one += time.perf_counter() - t0
+        s.close()
+    return {"sims": count, "sites": sites, "steps": steps,
+            "batched_f16_GLUPS": sites * steps / el / 1e9,
+            "one_by_one_f64_GLUPS": sites * baseline_steps / t_one / 1e9,
+            "nonfinite_sims": nan}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("which", choices=["precision", "dendrite", "sweep"])
+    ap.add_argument("--n", type=int, default=0)
+    ap.add_argument("--steps", type=int, default=0)
+    a = ap.parse_args()
+    build.build()
+    kw = {}
+    if a.n:
+        kw["n"] = a.n
+    if a.steps:
+        kw["steps"] = a.steps
+    fn = {"precision": precision, "dendrite": dendrite, "sweep": sweep}[a.which]
+    print(json.dumps(fn(**kw)))
+
+
+if __name__ == "__main__":
+    main()
