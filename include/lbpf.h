@@ -152,7 +152,7 @@ int64_t lbpf_steps_done(const lbpf_sim* sim);
 int lbpf_save(lbpf_sim* sim, const char* path);
 int lbpf_load(lbpf_sim* sim, const char* path);
 
-/* Tiling of the step kernels: node rows per block `by` (4..16; a block is
+/* Tiling of the step kernels: node rows per block `by` (4..8; a block is
  * 32 x by threads, one node per thread and plane) and z-chunk length
  * (>= 1; the z range is split into chunks processed by separate thread
  * blocks).  0 keeps the current value.  Takes effect at the next lbpf_step

@@ -90,7 +90,7 @@ struct lbpf_sim {
   SimDev* dd = nullptr;
   WorkItem* d_items = nullptr;
   int nitems = 0;
-  int by = 16, zchunk = 0;
+  int by = MAX_BLOCK_ROWS, zchunk = 0;
   double* d_part = nullptr;  // reduction partials + 4 results
   int npart = 0;
   double* d_small = nullptr; // tip output
@@ -112,7 +112,7 @@ struct lbpf_batch {
   SimDev* dd = nullptr;
   WorkItem* d_items = nullptr;
   int nitems = 0;
-  int by = 16;
+  int by = MAX_BLOCK_ROWS;
   StepLaunch fphi = nullptr, futh = nullptr;
   size_t smem_phi = 0, smem_uth = 0;
   cudaGraphExec_t gexec = nullptr;
@@ -681,7 +681,7 @@ int lbpf_get_state(lbpf_sim* s, double* g, double* h, double* f) {
 }
 
 int lbpf_set_tiling(lbpf_sim* s, int32_t by, int32_t zchunk) {
-  if (!s || by < 0 || zchunk < 0 || (by && (by < 4 || by > 16))) return LBPF_EINVAL;
+  if (!s || by < 0 || zchunk < 0 || (by && (by < 4 || by > MAX_BLOCK_ROWS))) return LBPF_EINVAL;
   if (s->sticky) return s->sticky;
   CK(s, cudaStreamSynchronize(s->stream));
   return apply_tiling(s, by ? by : s->by, zchunk ? zchunk : (by ? 0 : s->zchunk));
@@ -724,7 +724,7 @@ int lbpf_autotune(lbpf_sim* s, int32_t steps, double* best_ms) {
   CK(s, cudaEventCreate(&e1));
   double best = 1e300;
   int bbest = by0, zbest = zc0;
-  const int bys[] = {8, 12, 16};
+  const int bys[] = {4, 6, 8};
   for (int by : bys) {
     if (by > s->g.ny + 2 && by != bys[0]) continue;
     const int zdef = default_zchunk(s->g.nx, s->g.ny, s->g.nz, by);
@@ -852,7 +852,7 @@ int lbpf_batch_create(int32_t n, lbpf_sim* const* sims, void* cuda_stream, lbpf_
   b->sims.assign(sims, sims + n);
   b->stream = cuda_stream ? (cudaStream_t)cuda_stream : sims[0]->stream;
   const KernelTable& t = *sims[0]->kt;
-  b->by = 16;
+  b->by = MAX_BLOCK_ROWS;
   std::vector<WorkItem> items;
   std::vector<SimDev> descs;
   for (int i = 0; i < n; ++i) {

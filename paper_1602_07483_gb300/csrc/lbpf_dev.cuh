@@ -238,6 +238,17 @@ struct WorkItem {
 };
 
 constexpr int TILE_X = 30;  // interior columns per block row (block x = 32)
+constexpr int MAX_BLOCK_ROWS = 8;  // blocks of at most 32 x 8 threads
+
+// Resident blocks per SM the step kernels are compiled for (register budget:
+// 65536 / (256 x blocks) registers per thread).  Measured on 512^3: k_phi runs
+// best at three blocks (80 registers); k_uth at two (at 80 registers it spills).
+#ifndef LBPF_PHI_MIN_BLOCKS
+#define LBPF_PHI_MIN_BLOCKS 3
+#endif
+#ifndef LBPF_UTH_MIN_BLOCKS
+#define LBPF_UTH_MIN_BLOCKS 2
+#endif
 
 // ---------------------------------------------------------------- anisotropy
 // a_s(n) and N = |grad phi|^2 a_s d a_s / d(grad phi) (Eq. TermesAnisotropes),
@@ -327,7 +338,7 @@ struct RingRegs {
 
 // ---------------------------------------------------------------- phase field
 template <int QP, typename S>
-__global__ void __launch_bounds__(512) k_phi(const SimDev* __restrict__ sims, const WorkItem* __restrict__ items,
+__global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_PHI_MIN_BLOCKS) k_phi(const SimDev* __restrict__ sims, const WorkItem* __restrict__ items,
                                                 int s6) {
   using C = Codec<S>;
   using T = typename C::T;
@@ -568,7 +579,7 @@ __global__ void __launch_bounds__(512) k_phi(const SimDev* __restrict__ sims, co
 
 // ---------------------------------------------------------------- U and theta
 template <int QU, int QT, typename S>
-__global__ void __launch_bounds__(512) k_uth(const SimDev* __restrict__ sims, const WorkItem* __restrict__ items,
+__global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_UTH_MIN_BLOCKS) k_uth(const SimDev* __restrict__ sims, const WorkItem* __restrict__ items,
                                                 int s6) {
   using C = Codec<S>;
   using T = typename C::T;
