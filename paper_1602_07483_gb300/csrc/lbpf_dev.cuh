@@ -31,6 +31,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace lbpf {
 
 // ---------------------------------------------------------------- lattices
@@ -404,7 +406,9 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_PHI_MIN_BLOCKS) k_ph
     const T* R0 = ring + slot4(zc) * RS;
     const T* Rp = ring + slot4(zc + 1) * RS;
     const T* Rm = ring + slot4(zc - 1) * RS;
-    auto collide_row = [&](const int r, T& acc0, T& acc1, T& acc2) {
+    auto collide_row = [&](auto row_kind, T& acc0, T& acc1, T& acc2) {
+      constexpr int KIND = decltype(row_kind)::value;  // 0 interior row, 1 top halo, 2 bottom halo
+      auto row_needs = [](int ey) { return KIND == 0 || (KIND == 1 && ey == 1) || (KIND == 2 && ey == -1); };
       const int ly = ty;
       const int y = it.y0 - 1 + ly;
       const bool in_xy = x >= 0 && x < nx && y >= 0 && y < ny;
@@ -424,6 +428,7 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_PHI_MIN_BLOCKS) k_ph
 #pragma unroll
           for (int i = 0; i < QP; ++i) {
             const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
+            if (!row_needs(ey)) continue;
             const T wi = (T)L::w(i);
             const unsigned own = (unsigned)i * NS + site;
             const unsigned off = (unsigned)(ez * (int)plane + ey * nx + ex);
@@ -440,6 +445,7 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_PHI_MIN_BLOCKS) k_ph
 #pragma unroll
           for (int i = 0; i < QP; ++i) {
             const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
+            if (!row_needs(ey)) continue;
             const T wi = (T)L::w(i);
             const int sx = x - ex, sy = y - ey, sz = zc - ez;
             const bool inside = sx >= 0 && sx < nx && sy >= 0 && sy < ny && sz >= 0 && sz < nz;
@@ -473,6 +479,7 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_PHI_MIN_BLOCKS) k_ph
 #pragma unroll
         for (int i = 0; i < QP; ++i) {
           const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
+          if (!row_needs(ey)) continue;
           const T wi = (T)L::w(i);
           const T eN = (T)ex * Nx + (T)ey * Ny + (T)ez * Nz;
           const T g0 = wi * (ph - eN * c_N);
@@ -484,43 +491,49 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_PHI_MIN_BLOCKS) k_ph
           if (ey != 0) sGb[YS::slot(i) * PS + ly * 32 + tx] = gs[i];
         }
       }
-      // populations with e_y = 0: from this lane or the x-neighbour lane (all lanes shuffle)
-      T sv[QP];
-#pragma unroll
-      for (int i = 0; i < QP; ++i) {
-        const int ex = L::ex(i), ey = L::ey(i);
-        sv[i] = gs[i];
-        if (ey == 0 && ex > 0) sv[i] = __shfl_up_sync(0xffffffffu, gs[i], 1);
-        if (ey == 0 && ex < 0) sv[i] = __shfl_down_sync(0xffffffffu, gs[i], 1);
-      }
-      if (icol) {
-        if (!bnd) {
-#pragma unroll
-          for (int i = 0; i < QP; ++i) {
-            const int ey = L::ey(i), ez = L::ez(i);
-            if (ey != 0) continue;
-            if (ez < 0) acc0 += sv[i];
-            else if (ez > 0) acc2 += sv[i];
-            else acc1 += sv[i];
-          }
-        } else {
-#pragma unroll
-          for (int i = 0; i < QP; ++i) {
-            const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
-            if (ey != 0) continue;
-            const int sx = x - ex, sz = zc - ez;
-            const bool sin = sx >= 0 && sx < nx;
-            if (sin) {
+      if (KIND == 0) {
+        // populations with e_y = 0: from this lane or the x-neighbour lane (all lanes shuffle)
+        T sv[QP];
+  #pragma unroll
+        for (int i = 0; i < QP; ++i) {
+          const int ex = L::ex(i), ey = L::ey(i);
+          sv[i] = gs[i];
+          if (ey == 0 && ex > 0) sv[i] = __shfl_up_sync(0xffffffffu, gs[i], 1);
+          if (ey == 0 && ex < 0) sv[i] = __shfl_down_sync(0xffffffffu, gs[i], 1);
+        }
+        if (icol) {
+          if (!bnd) {
+  #pragma unroll
+            for (int i = 0; i < QP; ++i) {
+              const int ey = L::ey(i), ez = L::ez(i);
+              if (ey != 0) continue;
               if (ez < 0) acc0 += sv[i];
               else if (ez > 0) acc2 += sv[i];
               else acc1 += sv[i];
             }
-            if (!sin || sz < 0 || sz >= nz) acc1 += gs[L::opp(i)];
+          } else {
+  #pragma unroll
+            for (int i = 0; i < QP; ++i) {
+              const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
+              if (!row_needs(ey)) continue;
+              if (ey != 0) continue;
+              const int sx = x - ex, sz = zc - ez;
+              const bool sin = sx >= 0 && sx < nx;
+              if (sin) {
+                if (ez < 0) acc0 += sv[i];
+                else if (ez > 0) acc2 += sv[i];
+                else acc1 += sv[i];
+              }
+              if (!sin || sz < 0 || sz >= nz) acc1 += gs[L::opp(i)];
+            }
           }
         }
       }
     };
-    collide_row(0, a0A, a1A, a2A);
+    // rows 0 and BY-1 are halo rows: they only feed the e_y = +1 / -1 populations to the block
+    if (ty == 0) collide_row(std::integral_constant<int, 1>{}, a0A, a1A, a2A);
+    else if (ty == BY - 1) collide_row(std::integral_constant<int, 2>{}, a0A, a1A, a2A);
+    else collide_row(std::integral_constant<int, 0>{}, a0A, a1A, a2A);
     // ring plane zc+2 (its slot last held plane zc-2), then prefetch zc+3
     if (zc + 2 <= zhi + 1) {
       pf.store(rm, ring + slot4(zc + 2) * RS, tid, nthr);
@@ -647,7 +660,9 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_UTH_MIN_BLOCKS) k_ut
     const T* R0 = ring + slot4(zc) * RS;
     const T* Rp = ring + slot4(zc + 1) * RS;
     const T* Rm = ring + slot4(zc - 1) * RS;
-    auto collide_row = [&](const int r, T& u0, T& u1, T& u2, T& t0, T& t1, T& t2) {
+    auto collide_row = [&](auto row_kind, T& u0, T& u1, T& u2, T& t0, T& t1, T& t2) {
+      constexpr int KIND = decltype(row_kind)::value;  // 0 interior row, 1 top halo, 2 bottom halo
+      auto row_needs = [](int ey) { return KIND == 0 || (KIND == 1 && ey == 1) || (KIND == 2 && ey == -1); };
       const int ly = ty;
       const int y = it.y0 - 1 + ly;
       const bool in_xy = x >= 0 && x < nx && y >= 0 && y < ny;
@@ -669,12 +684,14 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_UTH_MIN_BLOCKS) k_ut
 #pragma unroll
           for (int i = 0; i < QU; ++i) {
             const int ex = LU::ex(i), ey = LU::ey(i), ez = LU::ez(i);
+            if (!row_needs(ey)) continue;
             const T sh = C::shifted ? (T)LU::w(i) * sh_h : T(0);
             hs[i] = C::dec(ldro(hin + ((unsigned)i * NS + site - (unsigned)(ez * (int)plane + ey * nx + ex))), sh, isc_h);
           }
 #pragma unroll
           for (int i = 0; i < QT; ++i) {
             const int ex = LT::ex(i), ey = LT::ey(i), ez = LT::ez(i);
+            if (!row_needs(ey)) continue;
             const T sh = C::shifted ? (T)LT::w(i) * sh_f : T(0);
             fs[i] = C::dec(ldro(fin + ((unsigned)i * NS + site - (unsigned)(ez * (int)plane + ey * nx + ex))), sh, isc_f);
           }
@@ -682,6 +699,7 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_UTH_MIN_BLOCKS) k_ut
 #pragma unroll
           for (int i = 0; i < QU; ++i) {
             const int ex = LU::ex(i), ey = LU::ey(i), ez = LU::ez(i);
+            if (!row_needs(ey)) continue;
             const int sx = x - ex, sy = y - ey, sz = zc - ez;
             const bool inside = sx >= 0 && sx < nx && sy >= 0 && sy < ny && sz >= 0 && sz < nz;
             const unsigned src = inside ? site - (unsigned)(ez * (int)plane + ey * nx + ex) : site;
@@ -692,6 +710,7 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_UTH_MIN_BLOCKS) k_ut
 #pragma unroll
           for (int i = 0; i < QT; ++i) {
             const int ex = LT::ex(i), ey = LT::ey(i), ez = LT::ez(i);
+            if (!row_needs(ey)) continue;
             const int sx = x - ex, sy = y - ey, sz = zc - ez;
             const bool inside = sx >= 0 && sx < nx && sy >= 0 && sy < ny && sz >= 0 && sz < nz;
             const unsigned src = inside ? site - (unsigned)(ez * (int)plane + ey * nx + ex) : site;
@@ -757,6 +776,7 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_UTH_MIN_BLOCKS) k_ut
 #pragma unroll
         for (int i = 0; i < QU; ++i) {
           const int ex = LU::ex(i), ey = LU::ey(i), ez = LU::ez(i);
+          if (!row_needs(ey)) continue;
           const T wi = (T)LU::w(i);
           const T sh = C::shifted ? wi * sh_h : T(0);
           const T eJ = (T)ex * Jx + (T)ey * Jy + (T)ez * Jz;
@@ -772,6 +792,7 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_UTH_MIN_BLOCKS) k_ut
 #pragma unroll
           for (int i = 0; i < QT; ++i) {
             const int ey = LT::ey(i);
+            if (!row_needs(ey)) continue;
             const T wi = (T)LT::w(i);
             const T sh = C::shifted ? wi * sh_f : T(0);
             const T f = fs[i] - (fs[i] - wi * th) * inv_etaT + wi * qth_dt;
@@ -782,71 +803,78 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_UTH_MIN_BLOCKS) k_ut
           }
         }
       }
-      // populations with e_y = 0: from this lane or the x-neighbour lane (all lanes shuffle)
-      T hv[QU], fv[QTA];
-#pragma unroll
-      for (int i = 0; i < QU; ++i) {
-        const int ex = LU::ex(i), ey = LU::ey(i);
-        hv[i] = hs[i];
-        if (ey == 0 && ex > 0) hv[i] = __shfl_up_sync(0xffffffffu, hs[i], 1);
-        if (ey == 0 && ex < 0) hv[i] = __shfl_down_sync(0xffffffffu, hs[i], 1);
-      }
-#pragma unroll
-      for (int i = 0; i < QT; ++i) {
-        const int ex = LT::ex(i), ey = LT::ey(i);
-        fv[i] = fs[i];
-        if (ey == 0 && ex > 0) fv[i] = __shfl_up_sync(0xffffffffu, fs[i], 1);
-        if (ey == 0 && ex < 0) fv[i] = __shfl_down_sync(0xffffffffu, fs[i], 1);
-      }
-      if (icol) {
-        if (inner) {
-#pragma unroll
-          for (int i = 0; i < QU; ++i) {
-            const int ey = LU::ey(i), ez = LU::ez(i);
-            if (ey != 0) continue;
-            if (ez < 0) u0 += hv[i];
-            else if (ez > 0) u2 += hv[i];
-            else u1 += hv[i];
-          }
-#pragma unroll
-          for (int i = 0; i < QT; ++i) {
-            const int ey = LT::ey(i), ez = LT::ez(i);
-            if (ey != 0) continue;
-            if (ez < 0) t0 += fv[i];
-            else if (ez > 0) t2 += fv[i];
-            else t1 += fv[i];
-          }
-        } else {
-#pragma unroll
-          for (int i = 0; i < QU; ++i) {
-            const int ex = LU::ex(i), ey = LU::ey(i), ez = LU::ez(i);
-            if (ey != 0) continue;
-            const int sx = x - ex, sz = zc - ez;
-            const bool sin = sx >= 0 && sx < nx;
-            if (sin) {
+      if (KIND == 0) {
+        // populations with e_y = 0: from this lane or the x-neighbour lane (all lanes shuffle)
+        T hv[QU], fv[QTA];
+  #pragma unroll
+        for (int i = 0; i < QU; ++i) {
+          const int ex = LU::ex(i), ey = LU::ey(i);
+          hv[i] = hs[i];
+          if (ey == 0 && ex > 0) hv[i] = __shfl_up_sync(0xffffffffu, hs[i], 1);
+          if (ey == 0 && ex < 0) hv[i] = __shfl_down_sync(0xffffffffu, hs[i], 1);
+        }
+  #pragma unroll
+        for (int i = 0; i < QT; ++i) {
+          const int ex = LT::ex(i), ey = LT::ey(i);
+          fv[i] = fs[i];
+          if (ey == 0 && ex > 0) fv[i] = __shfl_up_sync(0xffffffffu, fs[i], 1);
+          if (ey == 0 && ex < 0) fv[i] = __shfl_down_sync(0xffffffffu, fs[i], 1);
+        }
+        if (icol) {
+          if (inner) {
+  #pragma unroll
+            for (int i = 0; i < QU; ++i) {
+              const int ey = LU::ey(i), ez = LU::ez(i);
+              if (ey != 0) continue;
               if (ez < 0) u0 += hv[i];
               else if (ez > 0) u2 += hv[i];
               else u1 += hv[i];
             }
-            if (!sin || sz < 0 || sz >= nz) u1 += hs[LU::opp(i)];
-          }
-#pragma unroll
-          for (int i = 0; i < QT; ++i) {
-            const int ex = LT::ex(i), ey = LT::ey(i), ez = LT::ez(i);
-            if (ey != 0) continue;
-            const int sx = x - ex, sz = zc - ez;
-            const bool sin = sx >= 0 && sx < nx;
-            if (sin) {
+  #pragma unroll
+            for (int i = 0; i < QT; ++i) {
+              const int ey = LT::ey(i), ez = LT::ez(i);
+              if (ey != 0) continue;
               if (ez < 0) t0 += fv[i];
               else if (ez > 0) t2 += fv[i];
               else t1 += fv[i];
             }
-            if (!sin || sz < 0 || sz >= nz) t1 += fs[LT::opp(i)];
+          } else {
+  #pragma unroll
+            for (int i = 0; i < QU; ++i) {
+              const int ex = LU::ex(i), ey = LU::ey(i), ez = LU::ez(i);
+              if (!row_needs(ey)) continue;
+              if (ey != 0) continue;
+              const int sx = x - ex, sz = zc - ez;
+              const bool sin = sx >= 0 && sx < nx;
+              if (sin) {
+                if (ez < 0) u0 += hv[i];
+                else if (ez > 0) u2 += hv[i];
+                else u1 += hv[i];
+              }
+              if (!sin || sz < 0 || sz >= nz) u1 += hs[LU::opp(i)];
+            }
+  #pragma unroll
+            for (int i = 0; i < QT; ++i) {
+              const int ex = LT::ex(i), ey = LT::ey(i), ez = LT::ez(i);
+              if (!row_needs(ey)) continue;
+              if (ey != 0) continue;
+              const int sx = x - ex, sz = zc - ez;
+              const bool sin = sx >= 0 && sx < nx;
+              if (sin) {
+                if (ez < 0) t0 += fv[i];
+                else if (ez > 0) t2 += fv[i];
+                else t1 += fv[i];
+              }
+              if (!sin || sz < 0 || sz >= nz) t1 += fs[LT::opp(i)];
+            }
           }
         }
       }
     };
-    collide_row(0, u0A, u1A, u2A, t0A, t1A, t2A);
+    // rows 0 and BY-1 are halo rows: they only feed the e_y = +1 / -1 populations to the block
+    if (ty == 0) collide_row(std::integral_constant<int, 1>{}, u0A, u1A, u2A, t0A, t1A, t2A);
+    else if (ty == BY - 1) collide_row(std::integral_constant<int, 2>{}, u0A, u1A, u2A, t0A, t1A, t2A);
+    else collide_row(std::integral_constant<int, 0>{}, u0A, u1A, u2A, t0A, t1A, t2A);
     if (zc + 2 <= zhi + 1) pf.store(rm, ring + slot4(zc + 2) * RS, tid, nthr);
     if (zc + 3 <= zhi + 1) pf.fetch(rm, phi1, zc + 3, nz, plane);
     __syncthreads();
