@@ -177,7 +177,7 @@ def run_own(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    sim = lbpf.Sim(w.grid, w.lattices, storage="f32", stream=st.cuda_stream, **w.params)
+    sim = lbpf.Sim(w.grid, w.lattices, storage=args.storage, stream=st.cuda_stream, **w.params)
     sim.init_seed(w.centres, w.radii, w.U0, w.theta0)
     if args.autotune:
         sim.autotune(steps=2)
@@ -199,7 +199,7 @@ def run_own(args):
     value = sites * args.steps * world / t_max / 1e9
     # roofline of the dominant kernel: algorithmic bytes = read + write of every population it owns
     q_phi, q_u, q_t = w.lattices
-    s_bytes = 4
+    s_bytes = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}[args.storage]
     bytes_uth = 2 * s_bytes * (q_u + q_t) * sites
     bytes_phi = 2 * s_bytes * q_phi * sites
     uth_ms = ms_uth / args.steps
@@ -263,9 +263,10 @@ def run_own(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "kh512_q19x3_f32", "grid": [args.n] * 3, "lattices": [q_phi, q_u, q_t],
-                       "storage": "f32", "anisotropy": "K41+K61 eps=-0.02 delta=0.015", "seeds": 4,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.storage == "f64" else "f32",
+            "data": "synthetic",
+            "config": {"workload": "kh%d_q19x3_%s" % (args.n, args.storage), "grid": [args.n] * 3,
+                       "lattices": [q_phi, q_u, q_t], "storage": args.storage, "anisotropy": "K41+K61 eps=-0.02 delta=0.015", "seeds": 4,
                        "l2": "inputs larger than L2 (%.1f GB of populations)" % (2 * s_bytes * 57 * sites / 1e9),
                        "tiling": {"block": [32, by], "zchunk": zchunk}, "parallelism": "replicas x%d" % world},
             "roofline": {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -324,6 +325,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--n", type=int, default=512, help="grid edge (the workload is defined at 512)")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "f64"],
+                    help="population storage (the headline line is f32)")
     ap.add_argument("--autotune", type=int, default=0)
     ap.add_argument("--variants", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")

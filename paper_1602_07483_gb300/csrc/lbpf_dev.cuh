@@ -294,6 +294,14 @@ __device__ __forceinline__ S ldro(const S* p) { return __ldg(p); }
 
 __device__ __forceinline__ int slot4(int z) { return (z + 4) & 3; }  // z >= -1
 
+// Products and sums that are never fused into an FMA: the collision loops are
+// instantiated per row kind, and these keep the rounding identical in every
+// instantiation (a node recomputed as a halo equals its owner's value bit for bit).
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+
 // 1/x: IEEE division in FP64, the hardware approximate reciprocal in FP32
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
@@ -476,14 +484,33 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_PHI_MIN_BLOCKS) k_ph
         const T inv_a2 = bnd ? T(1) : rcp(a2);
         const T oma2 = T(1) - a2;
         const bool store = icol && zc >= it.z0 && zc < it.z1;
+        // g* = [g (1 - 1/eta) - (1 - a^2) g_nl + g0/eta + w Q dt/tau0] / a^2 with
+        // g0 = w (phi - e.N c_N): per weight class (rest, axis, diagonal) the terms
+        // without e_i are one constant, and the e.N part is a signed sum of scaled N
+        const T omw = T(1) - inv_eta;
+        const T kph = radd(rmul(inv_eta, ph), Qdt);
+        const T ncN = rmul(inv_eta, c_N);
+        T Kc[3], nxc[3], nyc[3], nzc[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const T wc = (T)L::w(c == 0 ? 0 : (c == 1 ? 1 : (QP > 7 ? 7 : 1)));
+          Kc[c] = rmul(wc, kph);
+          const T nc = rmul(-wc, ncN);
+          nxc[c] = rmul(nc, Nx);
+          nyc[c] = rmul(nc, Ny);
+          nzc[c] = rmul(nc, Nz);
+        }
 #pragma unroll
         for (int i = 0; i < QP; ++i) {
           const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
           if (!row_needs(ey)) continue;
+          const int c = i == 0 ? 0 : (i <= 6 ? 1 : 2);
           const T wi = (T)L::w(i);
-          const T eN = (T)ex * Nx + (T)ey * Ny + (T)ez * Nz;
-          const T g0 = wi * (ph - eN * c_N);
-          const T g = (gpull[i] - oma2 * gnl[i] - (gpull[i] - g0) * inv_eta + wi * Qdt) * inv_a2;
+          T eq = Kc[c];
+          if (ex) eq = radd(eq, ex > 0 ? nxc[c] : -nxc[c]);
+          if (ey) eq = radd(eq, ey > 0 ? nyc[c] : -nyc[c]);
+          if (ez) eq = radd(eq, ez > 0 ? nzc[c] : -nzc[c]);
+          const T g = rmul(fma(-oma2, gnl[i], fma(gpull[i], omw, eq)), inv_a2);
           const T shift_out = C::shifted ? wi * ph : T(0);
           const auto enc = C::enc(g, shift_out, scale);
           if (store) gout[(unsigned)i * NS + site] = enc;
@@ -773,29 +800,48 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_UTH_MIN_BLOCKS) k_ut
         const T src_dt = (Ssrc + fU * T(0.5) * dphidt * izc) * dt;
         const T qzU = qzc * U;
         const bool store = icol && zc >= it.z0 && zc < it.z1;
+        // h* = h (1 - 1/eta_U) + h0/eta_U + w (S + Q_U/zeta) dt with
+        // h0 = A U + B (q/zeta U + e.J c_J): per weight class one constant plus e.(scaled J)
+        const T omU = T(1) - inv_etaU;
+        T KU[3], jxc[3], jyc[3], jzc[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const int ic = c == 0 ? 0 : (c == 1 ? 1 : (QU > 7 ? 7 : 1));
+          const T wc = (T)LU::w(ic), Bc = (T)LU::B(ic);
+          KU[c] = radd(rmul(inv_etaU, radd(c == 0 ? U : T(0), rmul(Bc, qzU))), rmul(wc, src_dt));
+          const T jc = rmul(rmul(inv_etaU, Bc), c_J);
+          jxc[c] = rmul(jc, Jx);
+          jyc[c] = rmul(jc, Jy);
+          jzc[c] = rmul(jc, Jz);
+        }
 #pragma unroll
         for (int i = 0; i < QU; ++i) {
           const int ex = LU::ex(i), ey = LU::ey(i), ez = LU::ez(i);
           if (!row_needs(ey)) continue;
+          const int c = i == 0 ? 0 : (i <= 6 ? 1 : 2);
           const T wi = (T)LU::w(i);
           const T sh = C::shifted ? wi * sh_h : T(0);
-          const T eJ = (T)ex * Jx + (T)ey * Jy + (T)ez * Jz;
-          const T h0 = (i == 0 ? U : T(0)) + (T)LU::B(i) * (qzU + eJ * c_J);
-          const T h = hs[i] - (hs[i] - h0) * inv_etaU + wi * src_dt;
+          T eq = KU[c];
+          if (ex) eq = radd(eq, ex > 0 ? jxc[c] : -jxc[c]);
+          if (ey) eq = radd(eq, ey > 0 ? jyc[c] : -jyc[c]);
+          if (ez) eq = radd(eq, ez > 0 ? jzc[c] : -jzc[c]);
+          const T h = fma(hs[i], omU, eq);
           const auto enc = C::enc(h, sh, sc_h);
           if (store) hout[(unsigned)i * NS + site] = enc;
           hs[i] = C::shifted ? C::dec(enc, sh, isc_h) : h;
           if (ey != 0) sHb[YU::slot(i) * PS + ly * 32 + tx] = hs[i];
         }
         if (QT > 0) {
-          const T qth_dt = T(0.5) * dphi;  // w_i Q_theta dt with Q_theta = dphi/dt / 2
+          // f* = f (1 - 1/eta_T) + w (theta/eta_T + Q_theta dt) with Q_theta dt = dphi / 2
+          const T omT = T(1) - inv_etaT;
+          const T kT = radd(rmul(inv_etaT, th), rmul(T(0.5), dphi));
 #pragma unroll
           for (int i = 0; i < QT; ++i) {
             const int ey = LT::ey(i);
             if (!row_needs(ey)) continue;
             const T wi = (T)LT::w(i);
             const T sh = C::shifted ? wi * sh_f : T(0);
-            const T f = fs[i] - (fs[i] - wi * th) * inv_etaT + wi * qth_dt;
+            const T f = fma(fs[i], omT, rmul(wi, kT));
             const auto enc = C::enc(f, sh, sc_f);
             if (store) fout[(unsigned)i * NS + site] = enc;
             fs[i] = C::shifted ? C::dec(enc, sh, isc_f) : f;

@@ -28,7 +28,9 @@ def _sync():
         pass
 
 
-def _tip_series(sim, centre, steps, every):
+def _tip_series(sim, centre, steps, every, stop_margin=None, n=None):
+    """Tip position every `every` steps; stops early once the tip is within
+    `stop_margin` nodes of the +x wall (the tip line then no longer crosses phi = 0)."""
     xs = []
     done = 0
     while done < steps:
@@ -37,47 +39,67 @@ def _tip_series(sim, centre, steps, every):
         done += k
         x, rho = sim.tip(centre)
         xs.append((done, x, rho))
+        if stop_margin is not None and (x < 0 or x > n - 1 - stop_margin):
+            break
     return xs
 
 
-def _velocity(series, dx, dt, last_steps):
-    """Mean tip speed (physical units) over the last `last_steps` steps of a tip series."""
-    end = series[-1]
-    start = min(series, key=lambda r: abs((end[0] - r[0]) - last_steps))
-    if start[1] < 0 or end[1] < 0 or end[0] == start[0]:
-        return None
-    return (end[1] - start[1]) * dx / ((end[0] - start[0]) * dt)
+def _velocity(series, dx, dt, window, end_step=None):
+    """Mean tip speed (physical units) over `window` steps ending at `end_step` (default:
+    the last sample whose tip is inside the domain)."""
+    valid = [r for r in series if r[1] >= 0]
+    if not valid:
+        return None, None
+    end = valid[-1] if end_step is None else min(valid, key=lambda r: abs(r[0] - end_step))
+    start = min(valid, key=lambda r: abs((end[0] - r[0]) - window))
+    if end[0] == start[0]:
+        return None, None
+    return (end[1] - start[1]) * dx / ((end[0] - start[0]) * dt), (start[0], end[0])
 
 
-def precision(n=256, steps=8000, every=100, linf_at=200, storages=("f64", "f32", "f16", "bf16")):
+def precision(n=256, steps=8000, every=50, linf_at=200, window=1000, storages=("f64", "f32", "f16", "bf16")):
+    """The coupled heat + solute workload in several storage precisions.  The FP64 run
+    stops once its tip nears the +x wall; the others then run exactly as many steps so
+    that velocities and radii are compared over the same window."""
     w = workloads.coupled_dendrite(n=n)
     c = [int(v) for v in w.centres[0]]
-    out = {"workload": w.name.replace("_f64", ""), "grid": n, "steps": steps, "dt": w.params["dt"], "runs": {}}
-    ref_fields = None
-    ref_v = None
+    out = {"workload": w.name.replace("_f64", ""), "grid": n, "steps_requested": steps, "dt": w.params["dt"],
+           "runs": {}}
+    ref_fields = ref_v = ref_rho = None
+    stop_at = steps
+    win = None
     for st in storages:
         s = lbpf.sim_from_workload(w, storage=st)
         s.step(linf_at)
         f200 = s.read_fields()
         _sync()
         t0 = time.perf_counter()
-        series = _tip_series(s, c, steps - linf_at, every)
+        if st == "f64":
+            series = [(linf_at + a, b, r) for a, b, r in _tip_series(s, c, steps - linf_at, every, 8, n)]
+            stop_at = series[-1][0]
+        else:
+            series = [(linf_at + a, b, r) for a, b, r in _tip_series(s, c, stop_at - linf_at, every)]
         _sync()
         el = time.perf_counter() - t0
-        v = _velocity(series, w.params["dx"], w.params["dt"], 2000)
-        r = {"GLUPS_incl_diagnostics": w.sites * (steps - linf_at) / el / 1e9,
-             "tip_velocity": v, "tip_x_final": series[-1][1], "tip_radius_final": series[-1][2],
+        if st == "f64":
+            v, win = _velocity(series, w.params["dx"], w.params["dt"], window)
+            end = win[1] if win else None
+        else:
+            v, _ = _velocity(series, w.params["dx"], w.params["dt"], window, end_step=win[1] if win else None)
+        rho = dict((a, r) for a, _, r in series).get(win[1] if win else -1, -1.0)
+        r = {"steps_run": series[-1][0], "GLUPS_incl_diagnostics": w.sites * (series[-1][0] - linf_at) / el / 1e9,
+             "tip_velocity": v, "velocity_window_steps": win, "tip_radius_at_window_end": rho,
              "sums_final": s.sums(check=False).tolist()}
         if st == "f64":
-            ref_fields, ref_v, ref_rho = f200, v, series[-1][2]
+            ref_fields, ref_v, ref_rho = f200, v, rho
         else:
             r["phi_linf_at_%d" % linf_at] = float(np.abs(f200[0] - ref_fields[0]).max())
             r["U_linf_at_%d" % linf_at] = float(np.abs(f200[1] - ref_fields[1]).max())
             r["theta_linf_at_%d" % linf_at] = float(np.abs(f200[2] - ref_fields[2]).max())
             if v is not None and ref_v:
                 r["tip_velocity_rel_err"] = v / ref_v - 1
-            if ref_rho and ref_rho > 0 and series[-1][2] > 0:
-                r["tip_radius_rel_err"] = series[-1][2] / ref_rho - 1
+            if ref_rho and ref_rho > 0 and rho > 0:
+                r["tip_radius_rel_err"] = rho / ref_rho - 1
         out["runs"][st] = r
         s.close()
         print(json.dumps({st: r}), file=sys.stderr, flush=True)
@@ -85,17 +107,21 @@ def precision(n=256, steps=8000, every=100, linf_at=200, storages=("f64", "f32",
 
 
 def dendrite(n=128, steps=5000, every=100):
-    out = {"grid": n, "steps": steps, "runs": {}}
+    """The single 3D dendrite with D3Q19 and with D3Q7 for phi: tip position every
+    `every` steps (until the tip nears the wall), tip speed over the last 1000 steps
+    before that, in physical units and as V d0 / D."""
+    out = {"grid": n, "steps_requested": steps, "runs": {}}
     for qphi in (19, 7):
         w = workloads.single_dendrite(q_phi=qphi).with_(grid=(n, n, n))
         c = [int(v) for v in w.centres[0]]
         s = lbpf.sim_from_workload(w, storage="f64")
-        series = _tip_series(s, c, steps, every)
-        # the seed also grows along -x and along y: report the tips along the three axes
+        series = _tip_series(s, c, steps, every, 8, n)
+        v, win = _velocity(series, w.params["dx"], w.params["dt"], 1000)
+        d0 = 5 * np.sqrt(2) / 8 * w.params["W0"] / w.params["lam"]
         out["runs"]["phi_D3Q%d" % qphi] = {
             "tip_series": [(k, round(x, 4), round(r, 4)) for k, x, r in series],
-            "tip_velocity_last_2000": _velocity(series, w.params["dx"], w.params["dt"], 2000),
-            "d0": 5 * np.sqrt(2) / 8 / w.params["lam"],
+            "tip_velocity": v, "velocity_window_steps": win,
+            "tip_velocity_d0_over_D": (v * d0 / w.params["D"]) if v else None, "d0": d0,
         }
         s.close()
     return out
