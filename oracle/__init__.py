@@ -114,7 +114,7 @@ def load(openmp: bool = True):
 
 
 def lattice(q: int):
-    """Return (e[q,3] int, w, A, B, e2, opp) as typed from the paper's Tables 1-2."""
+    """Return (e[q,3] int, w, A, B, e2, opp) as typed from the paper's Tables 1-4 (2D lattices with e_z = 0)."""
     L = load()
     e = np.zeros((q, 3), np.int32)
     w, A, B = np.zeros(q), np.zeros(q), np.zeros(q)

@@ -55,6 +55,12 @@ static const int32_t E19[19][3] = {
     {-1, -1, 0}, {1, 0, 1}, {-1, 0, 1},  {1, 0, -1},  {-1, 0, -1},
     {0, 1, 1},  {0, -1, 1}, {0, 1, -1},  {0, -1, -1}};
 
+/* 2D lattices of Tables 3-4 (Sec. 3.4), stored with e_z = 0 so that an nz = 1 grid
+ * runs the paper's 2D scheme */
+static const int32_t E5[5][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {-1, 0, 0}, {0, -1, 0}};
+static const int32_t E9[9][3] = {{0, 0, 0},  {1, 0, 0},  {0, 1, 0},   {-1, 0, 0}, {0, -1, 0},
+                                 {1, 1, 0},  {-1, 1, 0}, {-1, -1, 0}, {1, -1, 0}};
+
 typedef struct {
   int q;
   int32_t e[19][3];
@@ -80,14 +86,24 @@ static int make_lattice(int q, lattice* L) {
     E = E19; L->e2 = 1.0 / 3.0;
     w0 = 1.0 / 3.0; w1 = 1.0 / 18.0; wd = 1.0 / 36.0;
     B0 = -2.0 / 3.0; B1 = 1.0 / 18.0; Bd = 1.0 / 36.0;
+  } else if (q == 5) {
+    E = E5; L->e2 = 1.0 / 3.0;
+    w0 = 1.0 / 3.0; w1 = 1.0 / 6.0; wd = 0.0;
+    B0 = -2.0 / 3.0; B1 = 1.0 / 6.0; Bd = 0.0;
+  } else if (q == 9) {
+    E = E9; L->e2 = 1.0 / 3.0;
+    w0 = 4.0 / 9.0; w1 = 1.0 / 9.0; wd = 1.0 / 36.0;
+    B0 = -5.0 / 9.0; B1 = 1.0 / 9.0; Bd = 1.0 / 36.0;
   } else {
     return -1;
   }
+  /* number of axis directions: 6 in 3D, 4 in 2D */
+  const int naxis = (q == 5 || q == 9) ? 4 : 6;
   for (int i = 0; i < q; ++i) {
     for (int a = 0; a < 3; ++a) L->e[i][a] = E[i][a];
-    L->w[i] = (i == 0) ? w0 : (i <= 6 ? w1 : wd);
+    L->w[i] = (i == 0) ? w0 : (i <= naxis ? w1 : wd);
     L->A[i] = (i == 0) ? 1.0 : 0.0;
-    L->B[i] = (i == 0) ? B0 : (i <= 6 ? B1 : Bd);
+    L->B[i] = (i == 0) ? B0 : (i <= naxis ? B1 : Bd);
   }
   /* opposite direction: the j with e_j = -e_i */
   for (int i = 0; i < q; ++i) {
@@ -319,8 +335,12 @@ static void grad_at(const ora_sim* s, const double* a, int x, int y, int z, doub
   g[2] = (a[IDX(s, x, y, mir(z + 1, s->nz))] - a[IDX(s, x, y, mir(z - 1, s->nz))]) * inv2dx;
 }
 
+/* boundary node (R4): on a wall that the phase-field lattice has links through
+ * (the 2D lattices have none through the z walls) */
 static inline int is_boundary(const ora_sim* s, int x, int y, int z) {
-  return x == 0 || y == 0 || z == 0 || x == s->nx - 1 || y == s->ny - 1 || z == s->nz - 1;
+  int zlinks = 0;
+  for (int i = 0; i < s->Lp.q; ++i) zlinks |= s->Lp.e[i][2] != 0;
+  return x == 0 || y == 0 || x == s->nx - 1 || y == s->ny - 1 || (zlinks && (z == 0 || z == s->nz - 1));
 }
 
 static inline int inside(const ora_sim* s, int x, int y, int z) {

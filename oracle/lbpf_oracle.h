@@ -35,7 +35,8 @@ typedef struct {
 
 typedef struct ora_sim ora_sim;
 
-/* Lattice tables (Tables 1 and 2 of Sec. 3.4).  q in {7, 15, 19}.
+/* Lattice tables (Tables 1-4 of Sec. 3.4).  q in {7, 15, 19} (3D) or {5, 9} (2D,
+ * stored with e_z = 0: an nz = 1 grid then runs the 2D scheme).
  * e: q*3 ints, w/A/B: q doubles, opp: q ints.  Returns 0, or -1 for a bad q. */
 int ora_lattice(int q, int32_t* e, double* w, double* A, double* B, double* e2, int32_t* opp);
 

@@ -16,7 +16,13 @@ import pytest
 import oracle
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden", "lattice_tables.json")
-LATS = {7: "D3Q7", 15: "D3Q15", 19: "D3Q19"}
+LATS = {7: "D3Q7", 15: "D3Q15", 19: "D3Q19", 5: "D2Q5", 9: "D2Q9"}
+ALL_Q = [7, 15, 19, 5, 9]
+
+
+def _dims(q):
+    """Spatial dimensions of the lattice: the 2D lattices are stored with e_z = 0."""
+    return 2 if q in (5, 9) else 3
 
 
 @pytest.fixture(scope="module")
@@ -25,7 +31,7 @@ def gold():
         return json.load(f)
 
 
-@pytest.mark.parametrize("q", [7, 15, 19])
+@pytest.mark.parametrize("q", ALL_Q)
 def test_tables_match_paper(gold, q):
     e, w, A, B, e2, opp = oracle.lattice(q)
     t = gold[LATS[q]]
@@ -36,7 +42,7 @@ def test_tables_match_paper(gold, q):
     np.testing.assert_array_equal(B, [float(Fraction(v)) for v in t["B"]])
 
 
-@pytest.mark.parametrize("q", [7, 15, 19])
+@pytest.mark.parametrize("q", ALL_Q)
 def test_lattice_identities_exact(gold, q):
     """Moment identities of Sec. 3 in exact rational arithmetic on the typed tables,
     and the same identities on the oracle's tables in floating point."""
@@ -46,12 +52,14 @@ def test_lattice_identities_exact(gold, q):
     A = [Fraction(v) for v in t["A"]]
     B = [Fraction(v) for v in t["B"]]
     e2 = Fraction(t["e2"])
+    d = _dims(q)
     assert sum(w) == 1
     assert sum(A) == 1
     assert sum(B) == 0
     for a in range(3):
         assert sum(wi * ei[a] for wi, ei in zip(w, e)) == 0
-        for b in range(3):
+    for a in range(d):
+        for b in range(d):
             assert sum(wi * ei[a] * ei[b] for wi, ei in zip(w, e)) == (e2 if a == b else 0)
             # first moment of the B-part of h^(0): sum B_i e_ia e_ib / e^2 = delta_ab (App. B)
             assert sum(Bi * ei[a] * ei[b] for Bi, ei in zip(B, e)) / e2 == (1 if a == b else 0)
@@ -60,10 +68,11 @@ def test_lattice_identities_exact(gold, q):
     # oracle floating tables satisfy the same identities
     eo, wo, Ao, Bo, e2o, opp = oracle.lattice(q)
     assert abs(wo.sum() - 1) < 1e-15
-    np.testing.assert_allclose(np.einsum("i,ia,ib->ab", wo, eo, eo), e2o * np.eye(3), atol=1e-15)
+    eye = np.diag([1.0] * d + [0.0] * (3 - d))
+    np.testing.assert_allclose(np.einsum("i,ia,ib->ab", wo, eo, eo), e2o * eye, atol=1e-15)
 
 
-@pytest.mark.parametrize("q", [7, 15, 19])
+@pytest.mark.parametrize("q", ALL_Q)
 def test_opposite_map(q):
     e, w, A, B, e2, opp = oracle.lattice(q)
     for i in range(q):
@@ -75,7 +84,7 @@ def test_opposite_map(q):
 def test_fourth_order_isotropy():
     """sum w e_x^4 = 3 sum w e_x^2 e_y^2 holds for D3Q15/D3Q19 and fails for D3Q7: the
     mechanism behind the paper's grid-anisotropy comparison (Sec. 4.1)."""
-    for q, iso in [(7, False), (15, True), (19, True)]:
+    for q, iso in [(7, False), (15, True), (19, True), (5, False), (9, True)]:
         e, w, *_ = oracle.lattice(q)
         m4 = float(np.sum(w * e[:, 0] ** 4))
         m22 = float(np.sum(w * e[:, 0] ** 2 * e[:, 1] ** 2))
@@ -159,35 +168,42 @@ def test_aniso_symmetries():
 
 # ---------------------------------------------------------------- equilibria
 
-@pytest.mark.parametrize("q", [7, 15, 19])
+@pytest.mark.parametrize("q", ALL_Q)
 def test_phase_equilibrium_moments(q):
-    """Sec. 3.2 / App. A: sum g0 = phi, sum g0 e = -N dt W0^2/(tau0 dx), sum g0 ee = e^2 phi I."""
+    """Sec. 3.2 / App. A: sum g0 = phi, sum g0 e = -N dt W0^2/(tau0 dx), sum g0 ee = e^2 phi I
+    (I restricted to the lattice's plane in 2D, where N has no z component)."""
     e, w, A, B, e2, opp = oracle.lattice(q)
+    d = _dims(q)
+    eye = np.diag([1.0] * d + [0.0] * (3 - d))
     rng = np.random.default_rng(q)
     for _ in range(20):
         phi = rng.uniform(-1, 1)
         N = rng.normal(size=3)
+        N[d:] = 0
         c = rng.uniform(0.001, 0.1)  # dt/dx W0^2/tau0
         g0 = oracle.geq(q, phi, N, c)
         assert abs(g0.sum() - phi) < 1e-14
         np.testing.assert_allclose(g0 @ e, -N * c, atol=1e-14)
-        np.testing.assert_allclose(np.einsum("i,ia,ib->ab", g0, e, e), e2 * phi * np.eye(3), atol=1e-14)
+        np.testing.assert_allclose(np.einsum("i,ia,ib->ab", g0, e, e), e2 * phi * eye, atol=1e-14)
 
 
-@pytest.mark.parametrize("q", [7, 15, 19])
+@pytest.mark.parametrize("q", ALL_Q)
 def test_solute_equilibrium_moments(q):
     """Sec. 3.3 / App. B: sum h0 = U, sum h0 e = J dt/dx, sum h0 ee = e^2 (q/zeta) U I."""
     e, w, A, B, e2, opp = oracle.lattice(q)
+    d = _dims(q)
+    eye = np.diag([1.0] * d + [0.0] * (3 - d))
     rng = np.random.default_rng(100 + q)
     for _ in range(20):
         U = rng.uniform(-1, 0.5)
         qz = rng.uniform(0, 1)
         J = rng.normal(size=3)
+        J[d:] = 0
         c = rng.uniform(0.001, 0.1)  # dt/dx
         h0 = oracle.heq(q, U, qz, J, c)
         assert abs(h0.sum() - U) < 1e-14
         np.testing.assert_allclose(h0 @ e, J * c, atol=1e-14)
-        np.testing.assert_allclose(np.einsum("i,ia,ib->ab", h0, e, e), e2 * qz * U * np.eye(3), atol=1e-14)
+        np.testing.assert_allclose(np.einsum("i,ia,ib->ab", h0, e, e), e2 * qz * U * eye, atol=1e-14)
 
 
 def test_paper_parameter_relations():
