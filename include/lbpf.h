@@ -12,7 +12,9 @@
  *     (RelaxationTime_Concentration), anti-trapping Eq. (AntiTrapping_Current);
  *   - theta: standard BGK with a source, Eqs. (LBE_Eq_Temp)-(ThermalDiffusivity);
  *   - streaming with bounce-back zero-flux walls (Sec. 3.4, Sec. 4).
- * Lattices D3Q7, D3Q15, D3Q19 (Tables 1-2).  One step is: phi collision and
+ * Lattices D3Q7, D3Q15, D3Q19 (Tables 1-2), or D2Q5, D2Q9 (Tables 3-4) on an
+ * nz = 1 grid, where the z walls carry no links and bound no wall nodes.
+ * One step is: phi collision and
  * streaming with phi^n, U^n, theta^n; then U and theta with phi^{n+1} and
  * dphi/dt = (phi^{n+1} - phi^n)/dt (Sec. 3.4, "Algorithm implementation").
  *
@@ -22,7 +24,7 @@
  *     returns LBPF_ECUDA.
  *   - Host arrays are owned by the caller, FP64, site-major with x fastest:
  *     index ((z*ny + y)*nx + x).  Population arrays are population-major,
- *     [Q][nz][ny][nx], in the paper's direction order (Table 1), and hold the
+ *     [Q][nz][ny][nx], in the paper's direction order (Table 1 or 3), and hold the
  *     POST-STREAMING populations g_i(x,t), h_i(x,t), f_i(x,t).
  *   - Device memory is owned by the handle (allocated in lbpf_create, freed
  *     in lbpf_destroy).  Work is enqueued on the caller's CUDA stream (or on
@@ -63,10 +65,12 @@ typedef struct {
   int32_t nx, ny, nz; /* nodes per edge, each >= 1; nx*ny*nz < 2^32 / 19 (226,050,910) */
 } lbpf_grid;
 
+/* 3D: every lattice in {7, 15, 19}.  2D: every lattice in {5, 9} and nz = 1.
+ * Mixing 2D and 3D lattices is LBPF_EINVAL. */
 typedef struct {
-  int32_t q_phi;   /* 7 | 15 | 19 */
-  int32_t q_u;     /* 7 | 15 | 19 */
-  int32_t q_theta; /* 0 (theta frozen at theta0) | 7 | 15 | 19 */
+  int32_t q_phi;   /* 7 | 15 | 19  or  5 | 9 */
+  int32_t q_u;     /* 7 | 15 | 19  or  5 | 9 */
+  int32_t q_theta; /* 0 (theta frozen at theta0) | 7 | 15 | 19  or  0 | 5 | 9 */
 } lbpf_lattice;
 
 typedef struct {
@@ -140,7 +144,8 @@ int lbpf_sums(lbpf_sim* sim, double out[4]);
  * phi_i >= 0 > phi_{i+1}, linearly interpolated, in lattice units (-1 when none).
  * rho (may be NULL): tip radius in lattice units from a least-squares parabola
  * x(j) = x_tip - j^2 / (2 rho) through the crossings of rows j = +-1..+-4 in the
- * xy and xz planes through the centre, averaged (-1 when undefined).  Synchronous. */
+ * xy and xz planes through the centre, averaged; on an nz = 1 grid the xy plane
+ * alone (-1 when undefined).  Synchronous. */
 int lbpf_tip(lbpf_sim* sim, const int32_t centre[3], double* x_tip, double* rho);
 
 /* Number of steps taken since the last init / set_state / load. */

@@ -561,7 +561,10 @@ double ora_tip(const ora_sim* s, int cx, int cy, int cz, double* rho) {
       }
       if (ok && num > 0.0) r[plane] = den / (2.0 * num); /* u = num/den, rho = 1/(2u) */
     }
-    *rho = (r[0] > 0.0 && r[1] > 0.0) ? 0.5 * (r[0] + r[1]) : -1.0;
+    if (s->nz == 1) /* 2D grid: the xy plane only */
+      *rho = r[0] > 0.0 ? r[0] : -1.0;
+    else
+      *rho = (r[0] > 0.0 && r[1] > 0.0) ? 0.5 * (r[0] + r[1]) : -1.0;
   }
   return xt;
 }

@@ -74,7 +74,8 @@ void ora_get_usource(const ora_sim* s, double* out);
 void ora_sums(const ora_sim* s, double out[4]);
 /* Tip along +x from node (cx, cy, cz): first crossing phi>=0>phi_next, linear
  * interpolation.  Returns x_tip (lattice units) or -1 when no crossing.
- * rho (may be NULL): tip radius in lattice units from the parabola fit. */
+ * rho (may be NULL): tip radius in lattice units from the parabola fit (xy and xz
+ * planes averaged; the xy plane alone on an nz = 1 grid). */
 double ora_tip(const ora_sim* s, int cx, int cy, int cz, double* rho);
 
 int64_t ora_steps_done(const ora_sim* s);

@@ -23,8 +23,12 @@ namespace {
 
 constexpr int kGraphSteps = 6;
 
-int q_index(int q) { return q == 7 ? 0 : (q == 15 ? 1 : (q == 19 ? 2 : -1)); }
-int qt_index(int q) { return q == 0 ? 0 : (q == 7 ? 1 : (q == 15 ? 2 : (q == 19 ? 3 : -1))); }
+// table slots: phi and U take a moving lattice, theta may also be 0 (frozen)
+int q_index(int q) {
+  const int s = lattice_slot(q);
+  return (s >= 0 && s < 5) ? s : -1;
+}
+int qt_index(int q) { return lattice_slot(q); }
 double lattice_e2(int q) { return q == 7 ? 0.25 : 1.0 / 3.0; }
 
 const KernelTable* table_for(int storage) {
@@ -234,6 +238,10 @@ int validate(const lbpf_grid* g, const lbpf_lattice* l, const lbpf_params* p) {
   const long long nsite = (long long)g->nx * g->ny * g->nz;
   if (nsite * 19 >= (1LL << 32)) return LBPF_EINVAL;
   if (q_index(l->q_phi) < 0 || q_index(l->q_u) < 0 || qt_index(l->q_theta) < 0) return LBPF_EINVAL;
+  // 2D lattices (D2Q5, D2Q9) run on an nz = 1 grid, all fields on 2D lattices
+  const bool d2 = lattice_is_2d(l->q_phi);
+  if (lattice_is_2d(l->q_u) != d2 || (l->q_theta && lattice_is_2d(l->q_theta) != d2)) return LBPF_EINVAL;
+  if (d2 && g->nz != 1) return LBPF_EINVAL;
   if (!(p->W0 > 0) || !(p->tau0 > 0) || !(p->D > 0) || !(p->dx > 0) || !(p->dt > 0)) return LBPF_EINVAL;
   if (l->q_theta && !(p->kappa > 0)) return LBPF_EINVAL;
   if (!(p->k > 0) || !(p->k <= 1)) return LBPF_EINVAL;

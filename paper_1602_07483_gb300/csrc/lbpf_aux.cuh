@@ -31,7 +31,13 @@ inline LatRT make_lat_rt_q() {
 }
 
 inline LatRT make_lat_rt(int q) {
-  return q == 7 ? make_lat_rt_q<7>() : (q == 15 ? make_lat_rt_q<15>() : make_lat_rt_q<19>());
+  switch (q) {
+    case 5: return make_lat_rt_q<5>();
+    case 7: return make_lat_rt_q<7>();
+    case 9: return make_lat_rt_q<9>();
+    case 15: return make_lat_rt_q<15>();
+    default: return make_lat_rt_q<19>();
+  }
 }
 
 __device__ __forceinline__ bool in_dom(int x, int y, int z, int nx, int ny, int nz) {
@@ -282,7 +288,9 @@ __global__ void k_tip(const T* __restrict__ phi, int nx, int ny, int nz, int cx,
       if (ok && num > 0) rho[plane] = den / (2.0 * num);
     }
     out[0] = xt;
-    out[1] = (rho[0] > 0 && rho[1] > 0) ? 0.5 * (rho[0] + rho[1]) : -1.0;
+    // a 2D grid (nz = 1) has the xy plane only
+    if (nz == 1) out[1] = rho[0] > 0 ? rho[0] : -1.0;
+    else out[1] = (rho[0] > 0 && rho[1] > 0) ? 0.5 * (rho[0] + rho[1]) : -1.0;
   }
 }
 

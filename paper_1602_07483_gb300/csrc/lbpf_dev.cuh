@@ -1,6 +1,7 @@
 // lbpf_dev.cuh -- device code of the lattice-Boltzmann phase-field step for sm_103a.
 //
-// One time step (Sec. 3.4, "Algorithm implementation") is two kernels:
+// One time step (Sec. 3.4, "Algorithm implementation") on D3Q7/D3Q15/D3Q19, or on
+// D2Q5/D2Q9 over an nz = 1 grid, is two kernels:
 //   k_phi : phi collision (Eq. collision stage, non-local term) + streaming with
 //           bounce-back, using phi^n, U^n, theta^n; writes the post-collision
 //           populations and phi^{n+1}.
@@ -43,6 +44,9 @@ struct Lat;
 template <>
 struct Lat<7> {
   static constexpr double e2 = 0.25;
+  static constexpr bool has_z = true;  // links through the z walls
+  static constexpr int diag0 = 1;      // first index of the diagonal weight class (none: an axis index)
+  __host__ __device__ static constexpr int cls(int i) { return i == 0 ? 0 : 1; }  // 0 rest, 1 axis, 2 diagonal
   __host__ __device__ static constexpr int ex(int i) { return i == 1 ? 1 : (i == 3 ? -1 : 0); }
   __host__ __device__ static constexpr int ey(int i) { return i == 2 ? 1 : (i == 4 ? -1 : 0); }
   __host__ __device__ static constexpr int ez(int i) { return i == 5 ? 1 : (i == 6 ? -1 : 0); }
@@ -58,6 +62,9 @@ struct Lat<7> {
 template <>
 struct Lat<15> {
   static constexpr double e2 = 1.0 / 3.0;
+  static constexpr bool has_z = true;
+  static constexpr int diag0 = 7;
+  __host__ __device__ static constexpr int cls(int i) { return i == 0 ? 0 : (i <= 6 ? 1 : 2); }
   // e_0..e_6 as D3Q7, then the cube diagonals
   __host__ __device__ static constexpr int ex(int i) {
     switch (i) {
@@ -99,6 +106,9 @@ struct Lat<15> {
 template <>
 struct Lat<19> {
   static constexpr double e2 = 1.0 / 3.0;
+  static constexpr bool has_z = true;
+  static constexpr int diag0 = 7;
+  __host__ __device__ static constexpr int cls(int i) { return i == 0 ? 0 : (i <= 6 ? 1 : 2); }
   // e_0..e_6 as D3Q7, then the twelve edge diagonals
   __host__ __device__ static constexpr int ex(int i) {
     switch (i) {
@@ -137,7 +147,59 @@ struct Lat<19> {
     return i == 0 ? -2.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
   }
 };
-// A_i = 1 for the rest population and 0 otherwise on all three lattices.
+// Table 3 (e_i) and Table 4 (w_i, A_i, B_i, e^2) of Sec. 3.4: the 2D lattices, run
+// on an nz = 1 grid (e_z = 0; no links through the z walls).
+template <>
+struct Lat<5> {
+  static constexpr double e2 = 1.0 / 3.0;
+  static constexpr bool has_z = false;
+  static constexpr int diag0 = 1;
+  __host__ __device__ static constexpr int cls(int i) { return i == 0 ? 0 : 1; }
+  __host__ __device__ static constexpr int ex(int i) { return i == 1 ? 1 : (i == 3 ? -1 : 0); }
+  __host__ __device__ static constexpr int ey(int i) { return i == 2 ? 1 : (i == 4 ? -1 : 0); }
+  __host__ __device__ static constexpr int ez(int) { return 0; }
+  __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : (i <= 2 ? i + 2 : i - 2); }
+  __host__ __device__ static constexpr double w(int i) { return i == 0 ? 1.0 / 3.0 : 1.0 / 6.0; }
+  __host__ __device__ static constexpr double B(int i) { return i == 0 ? -2.0 / 3.0 : 1.0 / 6.0; }
+};
+
+template <>
+struct Lat<9> {
+  static constexpr double e2 = 1.0 / 3.0;
+  static constexpr bool has_z = false;
+  static constexpr int diag0 = 5;
+  __host__ __device__ static constexpr int cls(int i) { return i == 0 ? 0 : (i <= 4 ? 1 : 2); }
+  // e_0..e_4 as D2Q5, then (1,1), (-1,1), (-1,-1), (1,-1)
+  __host__ __device__ static constexpr int ex(int i) {
+    switch (i) {
+      case 1: case 5: case 8: return 1;
+      case 3: case 6: case 7: return -1;
+      default: return 0;
+    }
+  }
+  __host__ __device__ static constexpr int ey(int i) {
+    switch (i) {
+      case 2: case 5: case 6: return 1;
+      case 4: case 7: case 8: return -1;
+      default: return 0;
+    }
+  }
+  __host__ __device__ static constexpr int ez(int) { return 0; }
+  __host__ __device__ static constexpr int opp(int i) {
+    switch (i) {
+      case 1: return 3; case 2: return 4; case 3: return 1; case 4: return 2;
+      case 5: return 7; case 6: return 8; case 7: return 5; case 8: return 6;
+      default: return 0;
+    }
+  }
+  __host__ __device__ static constexpr double w(int i) {
+    return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+  }
+  __host__ __device__ static constexpr double B(int i) {
+    return i == 0 ? -5.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+  }
+};
+// A_i = 1 for the rest population and 0 otherwise on all five lattices.
 
 // Populations with e_y != 0 cross block rows during the moment gather and go
 // through shared memory; yslot(i) numbers them 0..NY-1 (-1 for e_y = 0).
@@ -423,7 +485,8 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_PHI_MIN_BLOCKS) k_ph
       const bool icol = in_xy && tx >= 1 && tx <= TILE_X && ly >= 1 && ly <= BY - 2;
       const int rc = (ly + 1) * RW + (tx + 1);
       const unsigned site = ((unsigned)zc * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
-      const bool bnd = x == 0 || y == 0 || zc == 0 || x == nx - 1 || y == ny - 1 || zc == nz - 1;
+      // wall node (standard collision): on a wall the lattice has links through
+      const bool bnd = x == 0 || y == 0 || x == nx - 1 || y == ny - 1 || (L::has_z && (zc == 0 || zc == nz - 1));
       T gs[QP];
 #pragma unroll
       for (int i = 0; i < QP; ++i) gs[i] = T(0);
@@ -493,7 +556,7 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_PHI_MIN_BLOCKS) k_ph
         T Kc[3], nxc[3], nyc[3], nzc[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const T wc = (T)L::w(c == 0 ? 0 : (c == 1 ? 1 : (QP > 7 ? 7 : 1)));
+          const T wc = (T)L::w(c == 0 ? 0 : (c == 1 ? 1 : L::diag0));
           Kc[c] = rmul(wc, kph);
           const T nc = rmul(-wc, ncN);
           nxc[c] = rmul(nc, Nx);
@@ -504,7 +567,7 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_PHI_MIN_BLOCKS) k_ph
         for (int i = 0; i < QP; ++i) {
           const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
           if (!row_needs(ey)) continue;
-          const int c = i == 0 ? 0 : (i <= 6 ? 1 : 2);
+          const int c = L::cls(i);
           const T wi = (T)L::w(i);
           T eq = Kc[c];
           if (ex) eq = radd(eq, ex > 0 ? nxc[c] : -nxc[c]);
@@ -577,7 +640,7 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_PHI_MIN_BLOCKS) k_ph
       const int y = it.y0 - 1 + ly;
       const bool icol = x >= 0 && x < nx && y >= 0 && y < ny && tx >= 1 && tx <= TILE_X && ly >= 1 && ly <= BY - 2;
       if (icol) {
-        const bool inner = x >= 1 && y >= 1 && zc >= 1 && x <= nx - 2 && y <= ny - 2 && zc <= nz - 2;
+        const bool inner = x >= 1 && y >= 1 && x <= nx - 2 && y <= ny - 2 && (!L::has_z || (zc >= 1 && zc <= nz - 2));
         if (inner) {
 #pragma unroll
           for (int i = 0; i < QP; ++i) {
@@ -696,7 +759,7 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_UTH_MIN_BLOCKS) k_ut
       const bool icol = in_xy && tx >= 1 && tx <= TILE_X && ly >= 1 && ly <= BY - 2;
       const int rc = (ly + 1) * RW + (tx + 1);
       const unsigned site = ((unsigned)zc * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
-      const bool inner = x >= 1 && y >= 1 && zc >= 1 && x <= nx - 2 && y <= ny - 2 && zc <= nz - 2;
+      const bool inner = x >= 1 && y >= 1 && x <= nx - 2 && y <= ny - 2 && (!LU::has_z || (zc >= 1 && zc <= nz - 2));
       T hs[QU], fs[QTA];
 #pragma unroll
       for (int i = 0; i < QU; ++i) hs[i] = T(0);
@@ -806,7 +869,7 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_UTH_MIN_BLOCKS) k_ut
         T KU[3], jxc[3], jyc[3], jzc[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const int ic = c == 0 ? 0 : (c == 1 ? 1 : (QU > 7 ? 7 : 1));
+          const int ic = c == 0 ? 0 : (c == 1 ? 1 : LU::diag0);
           const T wc = (T)LU::w(ic), Bc = (T)LU::B(ic);
           KU[c] = radd(rmul(inv_etaU, radd(c == 0 ? U : T(0), rmul(Bc, qzU))), rmul(wc, src_dt));
           const T jc = rmul(rmul(inv_etaU, Bc), c_J);
@@ -818,7 +881,7 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_UTH_MIN_BLOCKS) k_ut
         for (int i = 0; i < QU; ++i) {
           const int ex = LU::ex(i), ey = LU::ey(i), ez = LU::ez(i);
           if (!row_needs(ey)) continue;
-          const int c = i == 0 ? 0 : (i <= 6 ? 1 : 2);
+          const int c = LU::cls(i);
           const T wi = (T)LU::w(i);
           const T sh = C::shifted ? wi * sh_h : T(0);
           T eq = KU[c];
@@ -929,7 +992,7 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_UTH_MIN_BLOCKS) k_ut
       const int y = it.y0 - 1 + ly;
       const bool icol = x >= 0 && x < nx && y >= 0 && y < ny && tx >= 1 && tx <= TILE_X && ly >= 1 && ly <= BY - 2;
       if (icol) {
-        const bool inner = x >= 1 && y >= 1 && zc >= 1 && x <= nx - 2 && y <= ny - 2 && zc <= nz - 2;
+        const bool inner = x >= 1 && y >= 1 && x <= nx - 2 && y <= ny - 2 && (!LU::has_z || (zc >= 1 && zc <= nz - 2));
         if (inner) {
 #pragma unroll
           for (int i = 0; i < QU; ++i) {

@@ -16,10 +16,12 @@ struct KernelTable {
   int sbytes;            // bytes per stored population
   int tbytes;            // bytes of the compute type
   bool shifted;          // FP16/BF16 codec
-  StepLaunch phi[3];     // q_phi = 7, 15, 19
-  StepLaunch uth[3][4];  // q_u = 7, 15, 19  x  q_theta = 0, 7, 15, 19
-  const void* phi_fn[3];
-  const void* uth_fn[3][4];
+  // indexed by lattice_slot(q): 7, 15, 19, 5, 9; theta additionally 0 (frozen) in the last slot.
+  // Only pairings of one dimension are instantiated (the others are null).
+  StepLaunch phi[5];
+  StepLaunch uth[5][6];
+  const void* phi_fn[5];
+  const void* uth_fn[5][6];
   cudaError_t (*init_scalar)(cudaStream_t, int nx, int ny, int nz, const double* cen, const double* rad, int nseed,
                              double c, void* out);
   cudaError_t (*init_pop)(cudaStream_t, const SimDev& sd, const LatRT& Lp, const LatRT& Lu, const LatRT& Lt,
@@ -40,8 +42,29 @@ const KernelTable& table_f32();
 const KernelTable& table_f16();
 const KernelTable& table_bf16();
 
+// slot of a lattice in the kernel tables: D3Q7, D3Q15, D3Q19, D2Q5, D2Q9, then q_theta = 0; -1 otherwise
+inline int lattice_slot(int q) {
+  switch (q) {
+    case 7: return 0;
+    case 15: return 1;
+    case 19: return 2;
+    case 5: return 3;
+    case 9: return 4;
+    case 0: return 5;
+    default: return -1;
+  }
+}
+inline bool lattice_is_2d(int q) { return q == 5 || q == 9; }
+
 // populations with e_y != 0 (they cross block rows in the moment gather)
-inline int ny_count(int q) { return q == 7 ? 2 : (q == 15 ? 10 : (q == 19 ? 10 : 0)); }
+inline int ny_count(int q) {
+  switch (q) {
+    case 5: case 7: return 2;
+    case 9: return 6;
+    case 15: case 19: return 10;
+    default: return 0;
+  }
+}
 
 // shared-memory bytes of the step kernels for a block of 32 x by threads: four ring planes of (by+2) x 34 scalars (eight with the
 // FP16/BF16 codec in k_phi) and a double-buffered plane of the e_y != 0 populations

@@ -83,18 +83,19 @@ KernelTable build_table() {
   t.sbytes = (int)sizeof(S);
   t.tbytes = (int)sizeof(typename Codec<S>::T);
   t.shifted = Codec<S>::shifted;
-  t.phi[0] = launch_phi<7, S>;
-  t.phi[1] = launch_phi<15, S>;
-  t.phi[2] = launch_phi<19, S>;
-  t.phi_fn[0] = (const void*)k_phi<7, S>;
-  t.phi_fn[1] = (const void*)k_phi<15, S>;
-  t.phi_fn[2] = (const void*)k_phi<19, S>;
-#define LBPF_UTH(a, qa, b, qb)                         \
-  t.uth[a][b] = launch_uth<qa, qb, S>;                 \
-  t.uth_fn[a][b] = (const void*)k_uth<qa, qb, S>;
-  LBPF_UTH(0, 7, 0, 0) LBPF_UTH(0, 7, 1, 7) LBPF_UTH(0, 7, 2, 15) LBPF_UTH(0, 7, 3, 19)
-  LBPF_UTH(1, 15, 0, 0) LBPF_UTH(1, 15, 1, 7) LBPF_UTH(1, 15, 2, 15) LBPF_UTH(1, 15, 3, 19)
-  LBPF_UTH(2, 19, 0, 0) LBPF_UTH(2, 19, 1, 7) LBPF_UTH(2, 19, 2, 15) LBPF_UTH(2, 19, 3, 19)
+#define LBPF_PHI(q)                                   \
+  t.phi[lattice_slot(q)] = launch_phi<q, S>;          \
+  t.phi_fn[lattice_slot(q)] = (const void*)k_phi<q, S>;
+  LBPF_PHI(7) LBPF_PHI(15) LBPF_PHI(19) LBPF_PHI(5) LBPF_PHI(9)
+#undef LBPF_PHI
+#define LBPF_UTH(qa, qb)                                                \
+  t.uth[lattice_slot(qa)][lattice_slot(qb)] = launch_uth<qa, qb, S>;    \
+  t.uth_fn[lattice_slot(qa)][lattice_slot(qb)] = (const void*)k_uth<qa, qb, S>;
+  LBPF_UTH(7, 0) LBPF_UTH(7, 7) LBPF_UTH(7, 15) LBPF_UTH(7, 19)
+  LBPF_UTH(15, 0) LBPF_UTH(15, 7) LBPF_UTH(15, 15) LBPF_UTH(15, 19)
+  LBPF_UTH(19, 0) LBPF_UTH(19, 7) LBPF_UTH(19, 15) LBPF_UTH(19, 19)
+  LBPF_UTH(5, 0) LBPF_UTH(5, 5) LBPF_UTH(5, 9)
+  LBPF_UTH(9, 0) LBPF_UTH(9, 5) LBPF_UTH(9, 9)
 #undef LBPF_UTH
   t.init_scalar = AuxImpl<S>::init_scalar;
   t.init_pop = AuxImpl<S>::init_pop;

@@ -3,6 +3,8 @@
     python -m paper_1602_07483_gb300.experiments precision   # 256^3 coupled run, FP64/FP32/FP16
     python -m paper_1602_07483_gb300.experiments dendrite    # 128^3, tip every 100 steps, D3Q19 and D3Q7 phi
     python -m paper_1602_07483_gb300.experiments sweep       # 64 uneven simulations, batched FP16 vs one-by-one FP64
+    python -m paper_1602_07483_gb300.experiments pure2d      # 2D benchmark of Sec. 4.1, V_p(t) per precision
+    python -m paper_1602_07483_gb300.experiments anisotropy  # grid anisotropy A_g of a 301^3 sphere, D3Q7/15/19
 
 Every number comes from the CUDA library through its C ABI; each run prints one
 JSON object.  FP32/FP16 errors are measured against the FP64 GPU path, which the
@@ -127,6 +129,78 @@ def dendrite(n=128, steps=5000, every=100):
     return out
 
 
+def pure2d(n=500, storages=("f64", "f32", "f16", "bf16")):
+    """The 2D pure-substance benchmark of Sec. 4.1 (Delta = 0.55, D2Q9 phi, D2Q5 theta):
+    tip position every 5 time units to t = 300 and V_p = V d0/kappa over the last 10
+    time units, per storage precision, against the paper's V_p(300) = 0.01735."""
+    w = workloads.pure_substance_2d(n=n)
+    dt, dx, d0, kappa = w.params["dt"], w.params["dx"], w.extra["d0"], w.params["kappa"]
+    out = {"workload": w.name.replace("_f64", ""), "grid": list(w.grid), "steps": w.steps,
+           "vp_paper_t300": w.extra["vp_paper_t300"], "runs": {}}
+    ref = None
+    for st in storages:
+        s = lbpf.sim_from_workload(w, storage=st)
+        _sync()
+        t0 = time.perf_counter()
+        xs = []
+        for k in range(w.tip_every, w.steps + 1, w.tip_every):
+            s.step(w.tip_every)
+            xs.append((k * dt, s.tip((0, 0, 0))[0]))
+        _sync()
+        el = time.perf_counter() - t0
+        s.close()
+        vp = {}
+        for t in (100.0, 200.0, 300.0):
+            d = dict((round(a, 6), b) for a, b in xs)
+            vp[t] = (d[round(t, 6)] - d[round(t - 10.0, 6)]) * dx / 10.0 * d0 / kappa
+        r = {"vp_t100": vp[100.0], "vp_t200": vp[200.0], "vp_t300": vp[300.0],
+             "vp_t300_rel_to_paper": vp[300.0] / w.extra["vp_paper_t300"] - 1,
+             "x_tip_t300": xs[-1][1], "GLUPS_incl_tip_every_625_steps": w.sites * w.steps / el / 1e9}
+        if st == "f64":
+            ref = vp[300.0]
+        else:
+            r["vp_t300_rel_to_f64"] = vp[300.0] / ref - 1
+        out["runs"][st] = r
+        print(json.dumps({st: r}), file=sys.stderr, flush=True)
+    return out
+
+
+def radii_100_110(phi, c):
+    """Radii of the phi = 0 surface from the centre node c along (1,0,0) and (1,1,0):
+    first crossing phi >= 0 > phi_next on the node line, linearly interpolated; the
+    (1,1,0) distance is sqrt2 times the node-step index.  Returns (R100, R110, A_g %)
+    with A_g = |R100 - R110| / (R100 + R110) x 100 (Sec. 4.1)."""
+    def crossing(line):
+        i = int(np.where((line[:-1] >= 0) & (line[1:] < 0))[0][0])
+        return i + line[i] / (line[i] - line[i + 1])
+    r100 = crossing(phi[c, c, c:])
+    m = min(phi.shape[1], phi.shape[2]) - c
+    r110 = np.sqrt(2.0) * crossing(np.array([phi[c, c + j, c + j] for j in range(m)]))
+    return float(r100), float(r110), float(abs(r100 - r110) / (r100 + r110) * 100)
+
+
+def anisotropy(n=301, storage="f32", steps=None):
+    """Grid anisotropy A_g of an isotropic growing sphere (Sec. 4.1) for the phase field on
+    D3Q7, D3Q15 and D3Q19, against the paper's 3.095 / 0.073 / 0.116 %."""
+    out = {"grid": n, "storage": storage, "runs": {}}
+    for q in (7, 15, 19):
+        w = workloads.grid_anisotropy(q_phi=q, n=n, storage=storage)
+        k = steps or w.steps
+        s = lbpf.sim_from_workload(w)
+        _sync()
+        t0 = time.perf_counter()
+        s.step(k)
+        phi = s.read_fields(lbpf.LBPF_PHI)[0]
+        el = time.perf_counter() - t0
+        s.close()
+        c = n // 2
+        r100, r110, ag = radii_100_110(phi, c)
+        out["runs"]["phi_D3Q%d" % q] = {"steps": k, "R100": r100, "R110": r110, "Ag_pct": ag,
+                                        "Ag_paper_pct": w.extra["Ag_paper_pct"], "seconds": el}
+        print(json.dumps({q: out["runs"]["phi_D3Q%d" % q]}), file=sys.stderr, flush=True)
+    return out
+
+
 def sweep(count=64, steps=2000, baseline_steps=200):
     sims = workloads.batch_sweep(count=count, storage="f16")
     sites = sum(w.sites for w in sims)
@@ -163,7 +237,7 @@ def sweep(count=64, steps=2000, baseline_steps=200):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["precision", "dendrite", "sweep"])
+    ap.add_argument("which", choices=["precision", "dendrite", "sweep", "pure2d", "anisotropy"])
     ap.add_argument("--n", type=int, default=0)
     ap.add_argument("--steps", type=int, default=0)
     a = ap.parse_args()
@@ -173,7 +247,8 @@ def main():
         kw["n"] = a.n
     if a.steps:
         kw["steps"] = a.steps
-    fn = {"precision": precision, "dendrite": dendrite, "sweep": sweep}[a.which]
+    fn = {"precision": precision, "dendrite": dendrite, "sweep": sweep, "pure2d": pure2d,
+          "anisotropy": anisotropy}[a.which]
     print(json.dumps(fn(**kw)))
 
 

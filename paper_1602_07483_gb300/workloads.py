@@ -111,6 +111,35 @@ def large_kh(n: int = 512, storage: str = "f32") -> Workload:
                     U0=-0.5, theta0=-0.3, steps=4000, storage=storage)
 
 
+def pure_substance_2d(n: int = 500, storage: str = "f64") -> Workload:
+    """The 2D anisotropic benchmark of Sec. 4.1 (pure substance, Delta = 0.55):
+    D2Q9 for phi, D2Q5 for theta, n^2 nodes (500^2 in the paper), dx = 0.4 W0,
+    dt = 0.008 tau0, kappa = 4, lambda* = kappa/a_2 = 6.3826 (zero kinetic
+    coefficient), eps_s = 0.05, a seed of radius 10 dx centred on the corner
+    (-1/2, -1/2) between the two mirror walls (quarter domain).  No solute coupling
+    (M c_inf = 0): U runs on D2Q5 but does not act on phi.  The paper quotes
+    V_p = V d0/kappa = 0.01735 at t = 300 (37,500 steps), d0 = 0.1385."""
+    p = dict(W0=1.0, tau0=1.0, D=1.0, kappa=4.0, lam=6.3826, Mc_inf=0.0, k=1.0, aniso=0, eps1=0.05, eps2=0.0,
+             dx=0.4, dt=0.008, antitrapping=0, grad2_min=1e-12)
+    return Workload("pure2d_%d_d2q9_d2q5_%s" % (n, storage), (n, n, 1), (9, 5, 5), p,
+                    np.array([[-0.5, -0.5, 0.0]]), np.array([10.0]), U0=0.0, theta0=-0.55, steps=37500,
+                    storage=storage, tip_every=625, extra={"d0": 0.1385, "vp_paper_t300": 0.01735})
+
+
+def grid_anisotropy(q_phi: int = 19, n: int = 301, delta: float = 0.25, storage: str = "f32") -> Workload:
+    """The isotropic-sphere test of Sec. 4.1 (grid anisotropy A_g): pure substance
+    (M c_inf = 0), eps_s = 0, n^3 nodes (301^3 in the paper), dx = 0.01, dt = 1.5e-5,
+    W0 = 0.01, tau0 = 1e-4, lambda = 10, kappa = 0.7, a centred seed of radius 8 l.u.,
+    compared at t = 10^4 dt.  The paper does not state the undercooling; Delta = 0.25.
+    The phase field runs on q_phi, theta on D3Q7 (U, uncoupled, on D3Q7)."""
+    p = dict(W0=0.01, tau0=1e-4, D=1.0, kappa=0.7, lam=10.0, Mc_inf=0.0, k=1.0, aniso=0, eps1=0.0, eps2=0.0,
+             dx=0.01, dt=1.5e-5, antitrapping=0, grad2_min=1e-12)
+    c, r = centred_seed(n, 8.0)
+    return Workload("iso%d_q%d_%s" % (n, q_phi, storage), (n, n, n), (q_phi, 7, 7), p, c, r, U0=0.0,
+                    theta0=-delta, steps=10000, storage=storage,
+                    extra={"Ag_paper_pct": {7: 3.095, 15: 0.073, 19: 0.116}[q_phi]})
+
+
 BATCH_EDGES = (48, 64, 80, 96)
 BATCH_K = (0.1, 0.15, 0.3)
 
@@ -139,6 +168,7 @@ def by_name(name: str) -> Workload:
         "dendrite128": single_dendrite,
         "coupled256": coupled_dendrite,
         "kh512": large_kh,
+        "pure2d": pure_substance_2d,
     }
     return table[name]()
 

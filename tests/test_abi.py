@@ -59,6 +59,10 @@ def test_rejects_invalid_arguments(lib):
     assert _create(dx=-1.0) == lbpf.LBPF_EINVAL
     assert _create(storage=7) == lbpf.LBPF_EINVAL
     assert _create(aniso=3) == lbpf.LBPF_EINVAL
+    # 2D lattices: nz = 1 and no mixing with 3D lattices
+    assert _create(lattices=(9, 5, 5), grid=(8, 8, 2), dx=0.4, dt=0.008) == lbpf.LBPF_EINVAL
+    assert _create(lattices=(9, 5, 7), grid=(8, 8, 1), dx=0.4, dt=0.008) == lbpf.LBPF_EINVAL
+    assert _create(lattices=(5, 9, 0), grid=(8, 8, 1), storage=7) == lbpf.LBPF_EINVAL
 
 
 def test_rejects_unstable_nonlocal_collision(lib):
@@ -75,5 +79,6 @@ def test_no_gpu_fails_loudly(lib):
     if torch.cuda.is_available():
         pytest.skip("GPU present")
     assert _create(eps1=0.05, dt=0.05) == lbpf.LBPF_ECUDA
+    assert _create(lattices=(9, 5, 5), grid=(8, 8, 1), dx=0.4, dt=0.008) == lbpf.LBPF_ECUDA  # valid 2D set
     with pytest.raises(lbpf.LbpfError):
         lbpf.Sim((8, 8, 8))

@@ -323,3 +323,23 @@ def test_full_size_sampled_parity_kh512_f32():
     gpu.step(12)
     b = gpu.sums()
     assert abs((b[2] - 0.5 * b[0]) - (a[2] - 0.5 * a[0])) < 1e-6 * w.sites
+
+
+def test_grid_anisotropy_sphere_matches_oracle():
+    """The isotropic-sphere set-up of Sec. 4.1 (pure substance, theta on D3Q7) on 51^3 for
+    400 steps, phi on D3Q7 and D3Q19: the GPU FP64 fields track the oracle's and give the
+    same grid-anisotropy coefficient A_g."""
+    from paper_1602_07483_gb300.experiments import radii_100_110
+    for q in (7, 19):
+        w = workloads.grid_anisotropy(q_phi=q, n=51, storage="f64")
+        ora = oracle.Sim(w.grid, w.lattices, params=oracle_params(w.params))
+        ora.init_seed(w.centres, w.radii, w.U0, w.theta0)
+        gpu = lbpf.sim_from_workload(w)
+        ora.step(400)
+        gpu.step(400)
+        pg, _, tg = gpu.read_fields()
+        po, _, to = ora.fields()
+        assert rel_err(pg, po) < 1e-10 and rel_err(tg, to) < 1e-10
+        ag_g = radii_100_110(pg, 25)[2]
+        ag_o = radii_100_110(po, 25)[2]
+        assert abs(ag_g - ag_o) < 1e-8, (ag_g, ag_o)
