@@ -160,7 +160,12 @@ int default_zchunk(int nx, int ny, int nz, int by) {
 int raise_smem_limit(const void* fn, int device) {
   int maxsm = 0;
   if (cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) return LBPF_ECUDA;
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm) != cudaSuccess) return LBPF_ECUDA;
+  // the dynamic limit plus the kernel's static shared memory may not exceed the opt-in maximum
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return LBPF_ECUDA;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm - (int)fa.sharedSizeBytes) !=
+      cudaSuccess)
+    return LBPF_ECUDA;
   return LBPF_OK;
 }
 

@@ -486,7 +486,10 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_PHI_MIN_BLOCKS) k_ph
       const int rc = (ly + 1) * RW + (tx + 1);
       const unsigned site = ((unsigned)zc * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
       // wall node (standard collision): on a wall the lattice has links through
-      const bool bnd = x == 0 || y == 0 || x == nx - 1 || y == ny - 1 || (L::has_z && (zc == 0 || zc == nz - 1));
+      // (for lattices with z links the predicates keep the order of the 3D-only kernels:
+      // the compiler's schedule of the step kernels is sensitive to it)
+      const bool bnd = L::has_z ? (x == 0 || y == 0 || zc == 0 || x == nx - 1 || y == ny - 1 || zc == nz - 1)
+                                : (x == 0 || y == 0 || x == nx - 1 || y == ny - 1);
       T gs[QP];
 #pragma unroll
       for (int i = 0; i < QP; ++i) gs[i] = T(0);
@@ -640,7 +643,8 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_PHI_MIN_BLOCKS) k_ph
       const int y = it.y0 - 1 + ly;
       const bool icol = x >= 0 && x < nx && y >= 0 && y < ny && tx >= 1 && tx <= TILE_X && ly >= 1 && ly <= BY - 2;
       if (icol) {
-        const bool inner = x >= 1 && y >= 1 && x <= nx - 2 && y <= ny - 2 && (!L::has_z || (zc >= 1 && zc <= nz - 2));
+        const bool inner = L::has_z ? (x >= 1 && y >= 1 && zc >= 1 && x <= nx - 2 && y <= ny - 2 && zc <= nz - 2)
+                                    : (x >= 1 && y >= 1 && x <= nx - 2 && y <= ny - 2);
         if (inner) {
 #pragma unroll
           for (int i = 0; i < QP; ++i) {
@@ -759,7 +763,8 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_UTH_MIN_BLOCKS) k_ut
       const bool icol = in_xy && tx >= 1 && tx <= TILE_X && ly >= 1 && ly <= BY - 2;
       const int rc = (ly + 1) * RW + (tx + 1);
       const unsigned site = ((unsigned)zc * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
-      const bool inner = x >= 1 && y >= 1 && x <= nx - 2 && y <= ny - 2 && (!LU::has_z || (zc >= 1 && zc <= nz - 2));
+      const bool inner = LU::has_z ? (x >= 1 && y >= 1 && zc >= 1 && x <= nx - 2 && y <= ny - 2 && zc <= nz - 2)
+                                   : (x >= 1 && y >= 1 && x <= nx - 2 && y <= ny - 2);
       T hs[QU], fs[QTA];
 #pragma unroll
       for (int i = 0; i < QU; ++i) hs[i] = T(0);
@@ -992,7 +997,8 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_UTH_MIN_BLOCKS) k_ut
       const int y = it.y0 - 1 + ly;
       const bool icol = x >= 0 && x < nx && y >= 0 && y < ny && tx >= 1 && tx <= TILE_X && ly >= 1 && ly <= BY - 2;
       if (icol) {
-        const bool inner = x >= 1 && y >= 1 && x <= nx - 2 && y <= ny - 2 && (!LU::has_z || (zc >= 1 && zc <= nz - 2));
+        const bool inner = LU::has_z ? (x >= 1 && y >= 1 && zc >= 1 && x <= nx - 2 && y <= ny - 2 && zc <= nz - 2)
+                                     : (x >= 1 && y >= 1 && x <= nx - 2 && y <= ny - 2);
         if (inner) {
 #pragma unroll
           for (int i = 0; i < QU; ++i) {

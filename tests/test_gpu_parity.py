@@ -200,10 +200,13 @@ def test_bf16_storage_runs_and_stays_close(tip_f64):
     assert abs(v / v64 - 1) < 0.10, (v, v64)
 
 
-def test_tiling_does_not_change_results():
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_tiling_does_not_change_results(storage):
+    """Bit-identical fields under another tiling (block rows and z-chunks), for each
+    single-precision storage: halo nodes recompute their owners' collisions exactly."""
     w = workloads.coupled_dendrite(n=40)
-    a = lbpf.sim_from_workload(w, storage="f32")
-    b = lbpf.sim_from_workload(w, storage="f32")
+    a = lbpf.sim_from_workload(w, storage=storage)
+    b = lbpf.sim_from_workload(w, storage=storage)
     b.set_tiling(5, 3)
     a.step(13)
     b.step(13)
