@@ -79,6 +79,7 @@ double min_effective_tau(int kind, double e1, double e2, double c_eta, double* a
 
 struct lbpf_sim {
   lbpf_grid g{};
+  lbpf_grid kg{};  // grid as the kernels see it: g, or (nx, 1, ny) for the 2D lattices (paper's y on the z axis)
   lbpf_lattice lat{};
   lbpf_params p{};
   const KernelTable* kt = nullptr;
@@ -136,7 +137,7 @@ struct lbpf_batch {
 namespace {
 
 void build_items(int sim_index, int nx, int ny, int nz, int by, int zchunk, std::vector<WorkItem>& out) {
-  const int ty = by - 2;
+  const int ty = by == 1 ? 1 : by - 2;  // interior rows per block: one-row blocks (2D) have no y halo
   for (int z0 = 0; z0 < nz; z0 += zchunk)
     for (int y0 = 0; y0 < ny; y0 += ty)
       for (int x0 = 0; x0 < nx; x0 += TILE_X) out.push_back(WorkItem{sim_index, x0, y0, z0, std::min(nz, z0 + zchunk)});
@@ -146,9 +147,14 @@ void build_items(int sim_index, int nx, int ny, int nz, int by, int zchunk, std:
 // blocks resident at any time work on neighbouring tiles, so the one-node
 // halos they re-read are found in L2 (measured best at 512^3 on GB300)
 int default_zchunk(int nx, int ny, int nz, int by) {
-  (void)nx;
   (void)ny;
-  (void)by;
+  if (by == 1) {
+    // one-row (2D) blocks are single warps: chunks of 8 to 32 rows, short enough to give
+    // about 24 blocks per SM of a 152-SM GB300 when the plane is small
+    const int xt = (nx + TILE_X - 1) / TILE_X;
+    const int want = (152 * 24 + xt - 1) / xt;
+    return std::min(std::max(nz, 1), std::min(32, std::max(8, (nz + want - 1) / want)));
+  }
   if (nz <= 48) return nz;
   const int chunks = (nz + 31) / 32;
   return (nz + chunks - 1) / chunks;
@@ -181,15 +187,16 @@ int set_smem_attrs(lbpf_sim* s) {
 
 int apply_tiling(lbpf_sim* s, int by, int zchunk) {
   const KernelTable& t = *s->kt;
+  if (lattice_is_2d(s->lat.q_phi)) by = 1;  // 2D: one-row blocks, no y halo
   s->by = by;
-  s->zchunk = zchunk > 0 ? zchunk : default_zchunk(s->g.nx, s->g.ny, s->g.nz, by);
+  s->zchunk = zchunk > 0 ? zchunk : default_zchunk(s->kg.nx, s->kg.ny, s->kg.nz, by);
   s->smem_phi = phi_smem_bytes(t, s->lat.q_phi, by);
   s->smem_uth = uth_smem_bytes(t, s->lat.q_u, s->lat.q_theta, by);
   int maxsm = 0;
   CK(s, cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device));
   if ((int)s->smem_phi > maxsm || (int)s->smem_uth > maxsm) return LBPF_EINVAL;
   std::vector<WorkItem> items;
-  build_items(0, s->g.nx, s->g.ny, s->g.nz, by, s->zchunk, items);
+  build_items(0, s->kg.nx, s->kg.ny, s->kg.nz, by, s->zchunk, items);
   if (s->d_items) cudaFree(s->d_items);
   s->d_items = nullptr;
   CK(s, cudaMalloc(&s->d_items, items.size() * sizeof(WorkItem)));
@@ -264,7 +271,7 @@ int validate(const lbpf_grid* g, const lbpf_lattice* l, const lbpf_params* p) {
 void fill_dev(lbpf_sim* s) {
   const lbpf_params& p = s->p;
   SimDev& d = s->hd;
-  d.nx = s->g.nx; d.ny = s->g.ny; d.nz = s->g.nz;
+  d.nx = s->kg.nx; d.ny = s->kg.ny; d.nz = s->kg.nz;
   d.q_theta = s->lat.q_theta;
   d.nsite = s->nsite;
   for (int b = 0; b < 2; ++b)
@@ -370,6 +377,7 @@ int lbpf_create(const lbpf_grid* grid, const lbpf_lattice* lattice, const lbpf_p
   s->p = *params;
   s->kt = table_for(params->storage);
   s->nsite = (long long)grid->nx * grid->ny * grid->nz;
+  s->kg = lattice_is_2d(lattice->q_phi) ? lbpf_grid{grid->nx, 1, grid->ny} : *grid;
   if (cudaGetDevice(&s->device) != cudaSuccess) { free_sim(s); return LBPF_ECUDA; }
   if (cuda_stream) {
     s->stream = (cudaStream_t)cuda_stream;
@@ -410,7 +418,7 @@ int lbpf_create(const lbpf_grid* grid, const lbpf_lattice* lattice, const lbpf_p
   s->fphi = s->kt->phi[q_index(lattice->q_phi)];
   s->futh = s->kt->uth[q_index(lattice->q_u)][qt_index(lattice->q_theta)];
   // 32 x 8 blocks: two resident blocks per SM at 128 registers per thread
-  const int by = std::min(8, std::max(4, grid->ny + 2));
+  const int by = lattice_is_2d(lattice->q_phi) ? 1 : std::min(8, std::max(4, grid->ny + 2));
   if ((rc = upload_dev(s)) != LBPF_OK || (rc = apply_tiling(s, by, 0)) != LBPF_OK) {
     free_sim(s);
     return rc;
@@ -443,12 +451,15 @@ int lbpf_init_seed(lbpf_sim* s, int32_t n, const double* centres, const double* 
   if (rc) return rc;
   double* d_seed = nullptr;
   CK(s, cudaMalloc(&d_seed, sizeof(double) * 4 * n));
-  CK(s, cudaMemcpyAsync(d_seed, centres, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s->stream));
+  std::vector<double> cen(centres, centres + 3 * n);
+  if (lattice_is_2d(s->lat.q_phi))  // kernel coordinates (x, z, y)
+    for (int m = 0; m < n; ++m) std::swap(cen[3 * m + 1], cen[3 * m + 2]);
+  CK(s, cudaMemcpy(d_seed, cen.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice));
   CK(s, cudaMemcpyAsync(d_seed + 3 * n, radii, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
   const double c = s->p.dx / (sqrt(2.0) * s->p.W0);
   // phi of the seeds into level 1 (scratch), populations at buffer 0, moments at level 0,
   // and level 2 (phi^{n-1} of the codec) = the seed profile used by the encoder.
-  CK(s, s->kt->init_scalar(s->stream, s->g.nx, s->g.ny, s->g.nz, d_seed, d_seed + 3 * n, n, c, s->phi[1]));
+  CK(s, s->kt->init_scalar(s->stream, s->kg.nx, s->kg.ny, s->kg.nz, d_seed, d_seed + 3 * n, n, c, s->phi[1]));
   const LatRT Lp = make_lat_rt(s->lat.q_phi), Lu = make_lat_rt(s->lat.q_u);
   LatRT Lt{};
   if (s->lat.q_theta) Lt = make_lat_rt(s->lat.q_theta);
@@ -575,8 +586,12 @@ int lbpf_sums(lbpf_sim* s, double out[4]) {
 int lbpf_tip(lbpf_sim* s, const int32_t centre[3], double* x_tip, double* rho) {
   if (!s || !centre || !x_tip) return LBPF_EINVAL;
   if (s->sticky) return s->sticky;
-  CK(s, s->kt->tip(s->stream, s->phi[s6_of(s) % 3], s->g.nx, s->g.ny, s->g.nz, centre[0], centre[1], centre[2],
-                   s->d_small));
+  // radius planes: both (xy, xz); the xy plane alone on an nz = 1 grid, which for the 2D
+  // lattices is the kernel's xz plane
+  const bool d2 = lattice_is_2d(s->lat.q_phi);
+  const int planes = d2 ? 2 : (s->g.nz == 1 ? 1 : 0);
+  CK(s, s->kt->tip(s->stream, s->phi[s6_of(s) % 3], s->kg.nx, s->kg.ny, s->kg.nz, centre[0], d2 ? centre[2] : centre[1],
+                   d2 ? centre[1] : centre[2], planes, s->d_small));
   CK(s, cudaMemcpyAsync(s->h_small, s->d_small, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   CK(s, cudaStreamSynchronize(s->stream));
   *x_tip = s->h_small[0];
@@ -739,9 +754,9 @@ int lbpf_autotune(lbpf_sim* s, int32_t steps, double* best_ms) {
   int bbest = by0, zbest = zc0;
   const int bys[] = {4, 6, 8};
   for (int by : bys) {
-    if (by > s->g.ny + 2 && by != bys[0]) continue;
-    const int zdef = default_zchunk(s->g.nx, s->g.ny, s->g.nz, by);
-    const int zcs[] = {zdef, std::max(8, zdef / 2), std::min(s->g.nz, zdef * 2), s->g.nz};
+    if (by > s->kg.ny + 2 && by != bys[0]) continue;
+    const int zdef = default_zchunk(s->kg.nx, s->kg.ny, s->kg.nz, by);
+    const int zcs[] = {zdef, std::max(8, zdef / 2), std::min(s->kg.nz, zdef * 2), s->kg.nz};
     for (int zc : zcs) {
       if (apply_tiling(s, by, zc) != LBPF_OK) { s->sticky = LBPF_OK; continue; }
       int rc = lbpf_step(s, 1);  // warm-up
@@ -865,7 +880,7 @@ int lbpf_batch_create(int32_t n, lbpf_sim* const* sims, void* cuda_stream, lbpf_
   b->sims.assign(sims, sims + n);
   b->stream = cuda_stream ? (cudaStream_t)cuda_stream : sims[0]->stream;
   const KernelTable& t = *sims[0]->kt;
-  b->by = MAX_BLOCK_ROWS;
+  b->by = lattice_is_2d(sims[0]->lat.q_phi) ? 1 : MAX_BLOCK_ROWS;
   std::vector<WorkItem> items;
   std::vector<SimDev> descs;
   for (int i = 0; i < n; ++i) {
@@ -873,7 +888,7 @@ int lbpf_batch_create(int32_t n, lbpf_sim* const* sims, void* cuda_stream, lbpf_
     cudaStreamSynchronize(s->stream);
     fill_dev(s);
     descs.push_back(s->hd);
-    build_items(i, s->g.nx, s->g.ny, s->g.nz, b->by, default_zchunk(s->g.nx, s->g.ny, s->g.nz, b->by), items);
+    build_items(i, s->kg.nx, s->kg.ny, s->kg.nz, b->by, default_zchunk(s->kg.nx, s->kg.ny, s->kg.nz, b->by), items);
   }
   // interleave large and small simulations: sort items by descending z-chunk work
   std::stable_sort(items.begin(), items.end(),

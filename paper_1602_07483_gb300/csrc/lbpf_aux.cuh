@@ -236,7 +236,7 @@ static __global__ void k_sums_final(const double* __restrict__ part, int nblk, d
 // phi_i >= 0 > phi_{i+1}: row 0 is (cy, cz); rows 1..8 are y = cy +- 1..4 at z = cz;
 // rows 9..16 are z = cz +- 1..4 at y = cy.  Thread 0 then fits the parabola.
 template <typename T>
-__global__ void k_tip(const T* __restrict__ phi, int nx, int ny, int nz, int cx, int cy, int cz,
+__global__ void k_tip(const T* __restrict__ phi, int nx, int ny, int nz, int cx, int cy, int cz, int planes,
                       double* __restrict__ out) {
   __shared__ double cross[17];
   const int r = threadIdx.y, lane = threadIdx.x;
@@ -288,8 +288,9 @@ __global__ void k_tip(const T* __restrict__ phi, int nx, int ny, int nz, int cx,
       if (ok && num > 0) rho[plane] = den / (2.0 * num);
     }
     out[0] = xt;
-    // a 2D grid (nz = 1) has the xy plane only
-    if (nz == 1) out[1] = rho[0] > 0 ? rho[0] : -1.0;
+    // planes: 0 both (averaged), 1 the xy plane alone, 2 the xz plane alone
+    if (planes == 1) out[1] = rho[0] > 0 ? rho[0] : -1.0;
+    else if (planes == 2) out[1] = rho[1] > 0 ? rho[1] : -1.0;
     else out[1] = (rho[0] > 0 && rho[1] > 0) ? 0.5 * (rho[0] + rho[1]) : -1.0;
   }
 }

@@ -44,7 +44,7 @@ struct Lat;
 template <>
 struct Lat<7> {
   static constexpr double e2 = 0.25;
-  static constexpr bool has_z = true;  // links through the z walls
+  static constexpr bool has_y = true;  // links along the kernel's y axis (false: a 2D lattice in the xz plane)
   static constexpr int diag0 = 1;      // first index of the diagonal weight class (none: an axis index)
   __host__ __device__ static constexpr int cls(int i) { return i == 0 ? 0 : 1; }  // 0 rest, 1 axis, 2 diagonal
   __host__ __device__ static constexpr int ex(int i) { return i == 1 ? 1 : (i == 3 ? -1 : 0); }
@@ -62,7 +62,7 @@ struct Lat<7> {
 template <>
 struct Lat<15> {
   static constexpr double e2 = 1.0 / 3.0;
-  static constexpr bool has_z = true;
+  static constexpr bool has_y = true;
   static constexpr int diag0 = 7;
   __host__ __device__ static constexpr int cls(int i) { return i == 0 ? 0 : (i <= 6 ? 1 : 2); }
   // e_0..e_6 as D3Q7, then the cube diagonals
@@ -106,7 +106,7 @@ struct Lat<15> {
 template <>
 struct Lat<19> {
   static constexpr double e2 = 1.0 / 3.0;
-  static constexpr bool has_z = true;
+  static constexpr bool has_y = true;
   static constexpr int diag0 = 7;
   __host__ __device__ static constexpr int cls(int i) { return i == 0 ? 0 : (i <= 6 ? 1 : 2); }
   // e_0..e_6 as D3Q7, then the twelve edge diagonals
@@ -147,17 +147,19 @@ struct Lat<19> {
     return i == 0 ? -2.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
   }
 };
-// Table 3 (e_i) and Table 4 (w_i, A_i, B_i, e^2) of Sec. 3.4: the 2D lattices, run
-// on an nz = 1 grid (e_z = 0; no links through the z walls).
+// Table 3 (e_i) and Table 4 (w_i, A_i, B_i, e^2) of Sec. 3.4: the 2D lattices.  A 2D
+// grid (nx, ny) runs as a kernel grid (nx, 1, ny): the paper's y axis becomes the
+// kernel's marching axis z, so ey() below is always 0 and ez() holds the paper's e_y.
+// Population order and memory layout are unchanged (one kernel plane row per paper row).
 template <>
 struct Lat<5> {
   static constexpr double e2 = 1.0 / 3.0;
-  static constexpr bool has_z = false;
+  static constexpr bool has_y = false;
   static constexpr int diag0 = 1;
   __host__ __device__ static constexpr int cls(int i) { return i == 0 ? 0 : 1; }
   __host__ __device__ static constexpr int ex(int i) { return i == 1 ? 1 : (i == 3 ? -1 : 0); }
-  __host__ __device__ static constexpr int ey(int i) { return i == 2 ? 1 : (i == 4 ? -1 : 0); }
-  __host__ __device__ static constexpr int ez(int) { return 0; }
+  __host__ __device__ static constexpr int ey(int) { return 0; }
+  __host__ __device__ static constexpr int ez(int i) { return i == 2 ? 1 : (i == 4 ? -1 : 0); }
   __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : (i <= 2 ? i + 2 : i - 2); }
   __host__ __device__ static constexpr double w(int i) { return i == 0 ? 1.0 / 3.0 : 1.0 / 6.0; }
   __host__ __device__ static constexpr double B(int i) { return i == 0 ? -2.0 / 3.0 : 1.0 / 6.0; }
@@ -166,10 +168,10 @@ struct Lat<5> {
 template <>
 struct Lat<9> {
   static constexpr double e2 = 1.0 / 3.0;
-  static constexpr bool has_z = false;
+  static constexpr bool has_y = false;
   static constexpr int diag0 = 5;
   __host__ __device__ static constexpr int cls(int i) { return i == 0 ? 0 : (i <= 4 ? 1 : 2); }
-  // e_0..e_4 as D2Q5, then (1,1), (-1,1), (-1,-1), (1,-1)
+  // paper's e_0..e_4 as D2Q5, then (1,1), (-1,1), (-1,-1), (1,-1); second component in ez()
   __host__ __device__ static constexpr int ex(int i) {
     switch (i) {
       case 1: case 5: case 8: return 1;
@@ -177,14 +179,14 @@ struct Lat<9> {
       default: return 0;
     }
   }
-  __host__ __device__ static constexpr int ey(int i) {
+  __host__ __device__ static constexpr int ey(int) { return 0; }
+  __host__ __device__ static constexpr int ez(int i) {
     switch (i) {
       case 2: case 5: case 6: return 1;
       case 4: case 7: case 8: return -1;
       default: return 0;
     }
   }
-  __host__ __device__ static constexpr int ez(int) { return 0; }
   __host__ __device__ static constexpr int opp(int i) {
     switch (i) {
       case 1: return 3; case 2: return 4; case 3: return 1; case 4: return 2;
@@ -302,7 +304,10 @@ struct WorkItem {
 };
 
 constexpr int TILE_X = 30;  // interior columns per block row (block x = 32)
-constexpr int MAX_BLOCK_ROWS = 8;  // blocks of at most 32 x 8 threads
+#ifndef LBPF_MAX_BLOCK_ROWS
+#define LBPF_MAX_BLOCK_ROWS 8
+#endif
+constexpr int MAX_BLOCK_ROWS = LBPF_MAX_BLOCK_ROWS;  // blocks of at most 32 x 8 threads
 
 // Resident blocks per SM the step kernels are compiled for (register budget:
 // 65536 / (256 x blocks) registers per thread).  Measured on 512^3: k_phi runs
@@ -437,7 +442,8 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_PHI_MIN_BLOCKS) k_ph
   const T* __restrict__ thn = (const T*)sd.th[par];
   const bool has_th = sd.q_theta != 0;
 
-  const int RW = 34, RS = RW * (BY + 2), PS = BY * 32;
+  constexpr bool HY = L::has_y;  // false: 2D lattice, one-row blocks without y halo
+  const int RW = 34, RS = HY ? RW * (BY + 2) : RW, PS = BY * 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ring = reinterpret_cast<T*>(smem_raw);  // phi^n     [4][BY+2][34]
   T* ringm = ring + 4 * RS;                  // phi^{n-1} [4][BY+2][34] (codec shift only)
@@ -480,16 +486,17 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_PHI_MIN_BLOCKS) k_ph
       constexpr int KIND = decltype(row_kind)::value;  // 0 interior row, 1 top halo, 2 bottom halo
       auto row_needs = [](int ey) { return KIND == 0 || (KIND == 1 && ey == 1) || (KIND == 2 && ey == -1); };
       const int ly = ty;
-      const int y = it.y0 - 1 + ly;
+      const int y = HY ? it.y0 - 1 + ly : it.y0 + ly;  // row 0 is a halo row except in one-row blocks
       const bool in_xy = x >= 0 && x < nx && y >= 0 && y < ny;
-      const bool icol = in_xy && tx >= 1 && tx <= TILE_X && ly >= 1 && ly <= BY - 2;
-      const int rc = (ly + 1) * RW + (tx + 1);
+      const bool icol = in_xy && tx >= 1 && tx <= TILE_X && (!HY || (ly >= 1 && ly <= BY - 2));
+      const int rc = HY ? (ly + 1) * RW + (tx + 1) : tx + 1;
       const unsigned site = ((unsigned)zc * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
       // wall node (standard collision): on a wall the lattice has links through
-      // (for lattices with z links the predicates keep the order of the 3D-only kernels:
-      // the compiler's schedule of the step kernels is sensitive to it)
-      const bool bnd = L::has_z ? (x == 0 || y == 0 || zc == 0 || x == nx - 1 || y == ny - 1 || zc == nz - 1)
-                                : (x == 0 || y == 0 || x == nx - 1 || y == ny - 1);
+      // wall node (standard collision) on a face the lattice has links through; for the 3D
+      // lattices the predicate keeps the order of the 3D-only kernels (the compiler's
+      // schedule of the step kernels is sensitive to it)
+      const bool bnd = L::has_y ? (x == 0 || y == 0 || zc == 0 || x == nx - 1 || y == ny - 1 || zc == nz - 1)
+                                : (x == 0 || zc == 0 || x == nx - 1 || zc == nz - 1);
       T gs[QP];
 #pragma unroll
       for (int i = 0; i < QP; ++i) gs[i] = T(0);
@@ -537,7 +544,7 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_PHI_MIN_BLOCKS) k_ph
         const T ph = R0[rc];
         // centred gradient with mirror ghosts (clamped ring)
         const T gx = (R0[rc + 1] - R0[rc - 1]) * inv2dx;
-        const T gy = (R0[rc + RW] - R0[rc - RW]) * inv2dx;
+        const T gy = HY ? (R0[rc + RW] - R0[rc - RW]) * inv2dx : T(0);
         const T gz = (Rp[rc] - Rm[rc]) * inv2dx;
         const T G2 = gx * gx + gy * gy + gz * gz;
         T as = 1, Nx = 0, Ny = 0, Nz = 0;
@@ -624,7 +631,8 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_PHI_MIN_BLOCKS) k_ph
       }
     };
     // rows 0 and BY-1 are halo rows: they only feed the e_y = +1 / -1 populations to the block
-    if (ty == 0) collide_row(std::integral_constant<int, 1>{}, a0A, a1A, a2A);
+    if (!HY) collide_row(std::integral_constant<int, 0>{}, a0A, a1A, a2A);
+    else if (ty == 0) collide_row(std::integral_constant<int, 1>{}, a0A, a1A, a2A);
     else if (ty == BY - 1) collide_row(std::integral_constant<int, 2>{}, a0A, a1A, a2A);
     else collide_row(std::integral_constant<int, 0>{}, a0A, a1A, a2A);
     // ring plane zc+2 (its slot last held plane zc-2), then prefetch zc+3
@@ -640,11 +648,11 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_PHI_MIN_BLOCKS) k_ph
     // populations with e_y != 0: from the neighbouring rows through shared memory
     auto gather_row = [&](const int r, T& acc0, T& acc1, T& acc2) {
       const int ly = ty;
-      const int y = it.y0 - 1 + ly;
-      const bool icol = x >= 0 && x < nx && y >= 0 && y < ny && tx >= 1 && tx <= TILE_X && ly >= 1 && ly <= BY - 2;
+      const int y = HY ? it.y0 - 1 + ly : it.y0 + ly;  // row 0 is a halo row except in one-row blocks
+      const bool icol = x >= 0 && x < nx && y >= 0 && y < ny && tx >= 1 && tx <= TILE_X && (!HY || (ly >= 1 && ly <= BY - 2));
       if (icol) {
-        const bool inner = L::has_z ? (x >= 1 && y >= 1 && zc >= 1 && x <= nx - 2 && y <= ny - 2 && zc <= nz - 2)
-                                    : (x >= 1 && y >= 1 && x <= nx - 2 && y <= ny - 2);
+        const bool inner = L::has_y ? (x >= 1 && y >= 1 && zc >= 1 && x <= nx - 2 && y <= ny - 2 && zc <= nz - 2)
+                                    : (x >= 1 && zc >= 1 && x <= nx - 2 && zc <= nz - 2);
         if (inner) {
 #pragma unroll
           for (int i = 0; i < QP; ++i) {
@@ -718,7 +726,8 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_UTH_MIN_BLOCKS) k_ut
   const T* __restrict__ thn = (const T*)sd.th[par];
   T* __restrict__ thnew = (T*)sd.th[par ^ 1];
 
-  const int RW = 34, RS = RW * (BY + 2), PS = BY * 32;
+  constexpr bool HY = LU::has_y;  // false: 2D lattices, one-row blocks without y halo
+  const int RW = 34, RS = HY ? RW * (BY + 2) : RW, PS = BY * 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ring = reinterpret_cast<T*>(smem_raw);  // phi^{n+1} [4][BY+2][34]
   T* sH = ring + 4 * RS;                     // [2][NYU + NYT][BY][32]
@@ -758,13 +767,13 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_UTH_MIN_BLOCKS) k_ut
       constexpr int KIND = decltype(row_kind)::value;  // 0 interior row, 1 top halo, 2 bottom halo
       auto row_needs = [](int ey) { return KIND == 0 || (KIND == 1 && ey == 1) || (KIND == 2 && ey == -1); };
       const int ly = ty;
-      const int y = it.y0 - 1 + ly;
+      const int y = HY ? it.y0 - 1 + ly : it.y0 + ly;  // row 0 is a halo row except in one-row blocks
       const bool in_xy = x >= 0 && x < nx && y >= 0 && y < ny;
-      const bool icol = in_xy && tx >= 1 && tx <= TILE_X && ly >= 1 && ly <= BY - 2;
-      const int rc = (ly + 1) * RW + (tx + 1);
+      const bool icol = in_xy && tx >= 1 && tx <= TILE_X && (!HY || (ly >= 1 && ly <= BY - 2));
+      const int rc = HY ? (ly + 1) * RW + (tx + 1) : tx + 1;
       const unsigned site = ((unsigned)zc * (unsigned)ny + (unsigned)y) * (unsigned)nx + (unsigned)x;
-      const bool inner = LU::has_z ? (x >= 1 && y >= 1 && zc >= 1 && x <= nx - 2 && y <= ny - 2 && zc <= nz - 2)
-                                   : (x >= 1 && y >= 1 && x <= nx - 2 && y <= ny - 2);
+      const bool inner = LU::has_y ? (x >= 1 && y >= 1 && zc >= 1 && x <= nx - 2 && y <= ny - 2 && zc <= nz - 2)
+                                   : (x >= 1 && zc >= 1 && x <= nx - 2 && zc <= nz - 2);
       T hs[QU], fs[QTA];
 #pragma unroll
       for (int i = 0; i < QU; ++i) hs[i] = T(0);
@@ -816,7 +825,7 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_UTH_MIN_BLOCKS) k_ut
         }
         // phi^{n+1} at the node and its six neighbours (mirror ghosts)
         const T pc = R0[rc];
-        const T pxp = R0[rc + 1], pxm = R0[rc - 1], pyp = R0[rc + RW], pym = R0[rc - RW], pzp = Rp[rc], pzm = Rm[rc];
+        const T pxp = R0[rc + 1], pxm = R0[rc - 1], pyp = HY ? R0[rc + RW] : pc, pym = HY ? R0[rc - RW] : pc, pzp = Rp[rc], pzm = Rm[rc];
         // q(phi) = (1 - phi)/2, zeta(phi) = ((1+k) - (1-k) phi)/2
         auto qf = [&](T p) { return T(0.5) * (T(1) - p); };
         // 1/zeta at the node and its six neighbours with one division (batch inversion):
@@ -986,7 +995,8 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_UTH_MIN_BLOCKS) k_ut
       }
     };
     // rows 0 and BY-1 are halo rows: they only feed the e_y = +1 / -1 populations to the block
-    if (ty == 0) collide_row(std::integral_constant<int, 1>{}, u0A, u1A, u2A, t0A, t1A, t2A);
+    if (!HY) collide_row(std::integral_constant<int, 0>{}, u0A, u1A, u2A, t0A, t1A, t2A);
+    else if (ty == 0) collide_row(std::integral_constant<int, 1>{}, u0A, u1A, u2A, t0A, t1A, t2A);
     else if (ty == BY - 1) collide_row(std::integral_constant<int, 2>{}, u0A, u1A, u2A, t0A, t1A, t2A);
     else collide_row(std::integral_constant<int, 0>{}, u0A, u1A, u2A, t0A, t1A, t2A);
     if (zc + 2 <= zhi + 1) pf.store(rm, ring + slot4(zc + 2) * RS, tid, nthr);
@@ -994,11 +1004,11 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_UTH_MIN_BLOCKS) k_ut
     __syncthreads();
     auto gather_row = [&](const int r, T& u0, T& u1, T& u2, T& t0, T& t1, T& t2) {
       const int ly = ty;
-      const int y = it.y0 - 1 + ly;
-      const bool icol = x >= 0 && x < nx && y >= 0 && y < ny && tx >= 1 && tx <= TILE_X && ly >= 1 && ly <= BY - 2;
+      const int y = HY ? it.y0 - 1 + ly : it.y0 + ly;  // row 0 is a halo row except in one-row blocks
+      const bool icol = x >= 0 && x < nx && y >= 0 && y < ny && tx >= 1 && tx <= TILE_X && (!HY || (ly >= 1 && ly <= BY - 2));
       if (icol) {
-        const bool inner = LU::has_z ? (x >= 1 && y >= 1 && zc >= 1 && x <= nx - 2 && y <= ny - 2 && zc <= nz - 2)
-                                     : (x >= 1 && y >= 1 && x <= nx - 2 && y <= ny - 2);
+        const bool inner = LU::has_y ? (x >= 1 && y >= 1 && zc >= 1 && x <= nx - 2 && y <= ny - 2 && zc <= nz - 2)
+                                     : (x >= 1 && zc >= 1 && x <= nx - 2 && zc <= nz - 2);
         if (inner) {
 #pragma unroll
           for (int i = 0; i < QU; ++i) {

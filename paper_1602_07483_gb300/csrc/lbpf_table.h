@@ -34,7 +34,8 @@ struct KernelTable {
   cudaError_t (*from_double)(cudaStream_t, void* out, const double* in, long long n);
   cudaError_t (*sums)(cudaStream_t, const void* phi, const void* U, const void* th, double theta0, double k,
                       long long n, double* part, int nblk);
-  cudaError_t (*tip)(cudaStream_t, const void* phi, int nx, int ny, int nz, int cx, int cy, int cz, double* out);
+  cudaError_t (*tip)(cudaStream_t, const void* phi, int nx, int ny, int nz, int cx, int cy, int cz, int planes,
+                     double* out);
 };
 
 const KernelTable& table_f64();
@@ -59,10 +60,9 @@ inline bool lattice_is_2d(int q) { return q == 5 || q == 9; }
 // populations with e_y != 0 (they cross block rows in the moment gather)
 inline int ny_count(int q) {
   switch (q) {
-    case 5: case 7: return 2;
-    case 9: return 6;
+    case 7: return 2;
     case 15: case 19: return 10;
-    default: return 0;
+    default: return 0;  // the 2D lattices have no kernel-y links
   }
 }
 

@@ -71,8 +71,8 @@ struct AuxImpl {
     return cudaGetLastError();
   }
   static cudaError_t tip(cudaStream_t st, const void* phi, int nx, int ny, int nz, int cx, int cy, int cz,
-                         double* out) {
-    k_tip<T><<<1, dim3(32, 17), 0, st>>>((const T*)phi, nx, ny, nz, cx, cy, cz, out);
+                         int planes, double* out) {
+    k_tip<T><<<1, dim3(32, 17), 0, st>>>((const T*)phi, nx, ny, nz, cx, cy, cz, planes, out);
     return cudaGetLastError();
   }
 };
