@@ -168,7 +168,10 @@ def run_own(args):
     build.build()
     st = torch.cuda.Stream()  # a real stream: the library enqueues on it and events are recorded on it
     torch.cuda.set_stream(st)
-    w = workloads.large_kh(args.n)
+    if args.workload == "pure2d":
+        w = workloads.pure_substance_2d(n=args.n if args.n != 512 else 8192, storage=args.storage)
+    else:
+        w = workloads.large_kh(args.n, storage=args.storage)
     hbm, peak_src = measured_peaks()
 
     def barrier_sync():
@@ -224,7 +227,7 @@ def run_own(args):
     e2e = None
     if rank == 0 or world > 1:
         ke = max(2, args.steps // 2)
-        phi_host = torch.empty((args.n, args.n, args.n), dtype=torch.float64, pin_memory=True).numpy()
+        phi_host = torch.empty(tuple(reversed(w.grid)), dtype=torch.float64, pin_memory=True).numpy()
         barrier_sync()
         t0 = time.perf_counter()
         sim.init_seed(w.centres, w.radii, w.U0, w.theta0)
@@ -249,11 +252,11 @@ def run_own(args):
     torch.cuda.empty_cache()
 
     variants = {}
-    if args.variants and rank == 0 and world == 1:
+    if args.variants and rank == 0 and world == 1 and args.workload == "kh":
         variants = run_variants(args, st)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu and args.workload == "kh":
         try:
             _, cpu = oracle_rate(budget_s=12.0, edge=64)
         except Exception as e:  # the CPU leg must not hide the GPU result
@@ -265,9 +268,13 @@ def run_own(args):
             "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.storage == "f64" else "f32",
             "data": "synthetic",
-            "config": {"workload": "kh%d_q19x3_%s" % (args.n, args.storage), "grid": [args.n] * 3,
-                       "lattices": [q_phi, q_u, q_t], "storage": args.storage, "anisotropy": "K41+K61 eps=-0.02 delta=0.015", "seeds": 4,
-                       "l2": "inputs larger than L2 (%.1f GB of populations)" % (2 * s_bytes * 57 * sites / 1e9),
+            "config": {"workload": w.name, "grid": list(w.grid),
+                       "lattices": [q_phi, q_u, q_t], "storage": args.storage,
+                       "anisotropy": ("K41+K61 eps=-0.02 delta=0.015" if args.workload == "kh"
+                                      else "cubic eps=0.05 (2D, Sec. 4.1 benchmark)"),
+                       "seeds": len(w.radii),
+                       "l2": "inputs larger than L2 (%.1f GB of populations)" % (
+                           2 * s_bytes * (q_phi + q_u + q_t) * sites / 1e9),
                        "tiling": {"block": [32, by], "zchunk": zchunk}, "parallelism": "replicas x%d" % world},
             "roofline": {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
@@ -341,6 +348,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--n", type=int, default=512, help="grid edge (the workload is defined at 512)")
+    ap.add_argument("--workload", default="kh", choices=["kh", "pure2d"],
+                    help="kh: the 512^3 D3Q19x3 two-harmonic dendrites (the headline); pure2d: the 2D "
+                         "Sec. 4.1 benchmark recipe on an n^2 plane (8192^2 unless --n is given)")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "f64"],
                     help="population storage (the headline line is f32)")
     ap.add_argument("--autotune", type=int, default=0)
