@@ -38,6 +38,21 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def job_rate(t_local, units_local, device="cuda"):
+    """Whole-job throughput of N ranks that each advance their own replica (weak scaling):
+    the units all ranks processed over the slowest rank's timed span.  Returns
+    (units / second, slowest span in seconds, total units)."""
+    import torch
+    t = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    if torch.distributed.is_available() and torch.distributed.is_initialized() and \
+            torch.distributed.get_world_size() > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(u, op=torch.distributed.ReduceOp.SUM)
+    t_max, units = float(t.item()), float(u.item())
+    return units / t_max, t_max, units
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -193,13 +208,9 @@ def run_own(args):
     ms_phi, ms_uth, ms_span = sim.step_timed(args.steps)
     barrier_sync()
     clk = clocks.stop()
-    t_local = ms_span / 1e3
-    t = torch.tensor([t_local], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    t_max = float(t.item())
     sites = w.sites
-    value = sites * args.steps * world / t_max / 1e9
+    rate, t_max, _ = job_rate(ms_span / 1e3, sites * args.steps)
+    value = rate / 1e9
     # roofline of the dominant kernel: algorithmic bytes = read + write of every population it owns
     q_phi, q_u, q_t = w.lattices
     s_bytes = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}[args.storage]
@@ -237,13 +248,10 @@ def run_own(args):
         sim.read_fields(lbpf.LBPF_PHI, out=[phi_host, None, None])
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        tt = torch.tensor([te], dtype=torch.float64, device="cuda")
-        if world > 1:
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        te = float(tt.item())
+        e2e_rate, _, _ = job_rate(te, sites * ke)
         h2d = (w.centres.size + w.radii.size) * 8 / ke
         d2h = 32 + sites * 8 / ke
-        e2e = {"value": sites * ke * world / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": e2e_rate / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": ke,
                "what": "lbpf_init_seed from host seeds, then per step lbpf_step(1) + lbpf_sums (D2H), "
                        "then lbpf_read_fields(phi) into pinned host memory"}
