@@ -44,7 +44,8 @@ __device__ __forceinline__ bool in_dom(int x, int y, int z, int nx, int ny, int 
   return x >= 0 && y >= 0 && z >= 0 && x < nx && y < ny && z < nz;
 }
 
-// phi of the diffuse seeds (Sec. 4): tanh((R - r) dx / (sqrt2 W0)), max over seeds.
+// phi of the diffuse seeds (Sec. 4): tanh((R - r) dx / (sqrt2 W0)), max over seeds
+// (tanh is increasing, so one tanh of the largest argument).
 template <typename T>
 __global__ void k_init_scalar(int nx, int ny, int nz, const double* __restrict__ cen, const double* __restrict__ rad,
                               int nseed, double c, T* __restrict__ out) {
@@ -53,13 +54,13 @@ __global__ void k_init_scalar(int nx, int ny, int nz, const double* __restrict__
     const int x = (int)(s % nx);
     const int y = (int)((s / nx) % ny);
     const int z = (int)(s / ((long long)nx * ny));
-    double ph = -1.0;
+    double arg = 0.0;
     for (int m = 0; m < nseed; ++m) {
       const double a = x - cen[3 * m], b = y - cen[3 * m + 1], d = z - cen[3 * m + 2];
-      const double v = tanh((rad[m] - sqrt(a * a + b * b + d * d)) * c);
-      if (m == 0 || v > ph) ph = v;
+      const double v = (rad[m] - sqrt(a * a + b * b + d * d)) * c;
+      if (m == 0 || v > arg) arg = v;
     }
-    out[s] = (T)ph;
+    out[s] = (T)(nseed > 0 ? tanh(arg) : -1.0);
   }
 }
 

@@ -318,6 +318,23 @@ constexpr int MAX_BLOCK_ROWS = LBPF_MAX_BLOCK_ROWS;  // blocks of at most 32 x 8
 #ifndef LBPF_UTH_MIN_BLOCKS
 #define LBPF_UTH_MIN_BLOCKS 2
 #endif
+// The 2D lattices run one-warp blocks; their launch bounds (counted in 256-thread
+// blocks) set the register budget that decides how many warps an SM holds.  Measured
+// on 8192^2 FP32: 64 registers (four 256-thread blocks) for both kernels, 21.2 -> 26.4
+// GLUPS.  FP64 has budgets of its own (at 64 registers it spills).
+#ifndef LBPF_PHI2D_MIN_BLOCKS
+#define LBPF_PHI2D_MIN_BLOCKS 4
+#endif
+#ifndef LBPF_UTH2D_MIN_BLOCKS
+#define LBPF_UTH2D_MIN_BLOCKS 4
+#endif
+// FP64 storage and arithmetic (values take two registers)
+#ifndef LBPF_PHI64_MIN_BLOCKS
+#define LBPF_PHI64_MIN_BLOCKS 3
+#endif
+#ifndef LBPF_UTH64_MIN_BLOCKS
+#define LBPF_UTH64_MIN_BLOCKS 2
+#endif
 
 // ---------------------------------------------------------------- anisotropy
 // a_s(n) and N = |grad phi|^2 a_s d a_s / d(grad phi) (Eq. TermesAnisotropes),
@@ -415,7 +432,8 @@ struct RingRegs {
 
 // ---------------------------------------------------------------- phase field
 template <int QP, typename S>
-__global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_PHI_MIN_BLOCKS) k_phi(const SimDev* __restrict__ sims, const WorkItem* __restrict__ items,
+__global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_PHI64_MIN_BLOCKS
+                                                       : (Lat<QP>::has_y ? LBPF_PHI_MIN_BLOCKS : LBPF_PHI2D_MIN_BLOCKS)) k_phi(const SimDev* __restrict__ sims, const WorkItem* __restrict__ items,
                                                 int s6) {
   using C = Codec<S>;
   using T = typename C::T;
@@ -694,7 +712,8 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_PHI_MIN_BLOCKS) k_ph
 
 // ---------------------------------------------------------------- U and theta
 template <int QU, int QT, typename S>
-__global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, LBPF_UTH_MIN_BLOCKS) k_uth(const SimDev* __restrict__ sims, const WorkItem* __restrict__ items,
+__global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_UTH64_MIN_BLOCKS
+                                                       : (Lat<QU>::has_y ? LBPF_UTH_MIN_BLOCKS : LBPF_UTH2D_MIN_BLOCKS)) k_uth(const SimDev* __restrict__ sims, const WorkItem* __restrict__ items,
                                                 int s6) {
   using C = Codec<S>;
   using T = typename C::T;
