@@ -113,24 +113,33 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+class OracleSample:
+    """The FP64 oracle on a bounded sample of the workload: an edge^3 box with the same
+    lattices and parameters and one seed.  rate() steps it until a time budget is used
+    and returns site-updates/s."""
+
+    def __init__(self, edge=64):
+        import oracle
+        from paper_1602_07483_gb300 import workloads
+        w = workloads.large_kh(512)
+        self.edge = edge
+        self.sim = oracle.Sim((edge, edge, edge), w.lattices, params=oracle.make_params(**dict(w.params)))
+        self.sim.init_seed([[edge / 2, edge / 2, edge / 2]], [6.0], w.U0, w.theta0)
+        self.sim.step(1)
+
+    def rate(self, budget_s):
+        steps, t0 = 0, time.perf_counter()
+        while True:
+            self.sim.step(1)
+            steps += 1
+            el = time.perf_counter() - t0
+            if el > budget_s or steps >= 400:
+                return self.edge ** 3 * steps / el, steps, el
+
+
 def oracle_rate(budget_s=12.0, edge=64, threads=None):
-    """FP64 oracle site-updates/s on a bounded sample of the workload: a edge^3 box with
-    the same lattices and parameters and one seed, stepped until the time budget is used."""
-    import oracle
-    from paper_1602_07483_gb300 import workloads
-    w = workloads.large_kh(512)
-    p = dict(w.params)
-    s = oracle.Sim((edge, edge, edge), w.lattices, params=oracle.make_params(**p))
-    s.init_seed([[edge / 2, edge / 2, edge / 2]], [6.0], w.U0, w.theta0)
-    s.step(1)
-    steps, t0 = 0, time.perf_counter()
-    while True:
-        s.step(1)
-        steps += 1
-        el = time.perf_counter() - t0
-        if el > budget_s or steps >= 400:
-            break
-    rate = edge ** 3 * steps / el
+    """FP64 oracle site-updates/s on a bounded sample of the workload (see OracleSample)."""
+    rate, steps, el = OracleSample(edge).rate(budget_s)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return rate / 1e9, {"value": rate / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
                         "sample": "%d^3 box of the 512^3 D3Q19x3 workload (same parameters, one seed), "
@@ -145,17 +154,26 @@ def run_reference(args):
     oracle.build()
     vals = []
     t_all = time.perf_counter()
+    # bounded samples of one 64^3 box: about 20 s of warm-up and 100 s of timed samples in all
+    sample = OracleSample(64)
     for _ in range(args.warmup):
-        oracle_rate(budget_s=2.0, edge=48)
+        sample.rate(max(0.1, min(2.0, 20.0 / max(1, args.warmup))))
+    total_steps, total_s = 0, 0.0
     for _ in range(args.steps):
-        v, _ = oracle_rate(budget_s=max(2.0, min(12.0, 60.0 / max(1, args.steps))), edge=64)
-        vals.append(v)
+        r, n, el = sample.rate(max(0.2, min(12.0, 100.0 / max(1, args.steps))))
+        vals.append(r / 1e9)
+        total_steps += n
+        total_s += el
     value = statistics.median(vals)
-    _, cb = oracle_rate(budget_s=1.0, edge=32)
-    cb["value"] = value
+    cb = {"value": value, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1)),
+          "kind": "oracle",
+          "sample": "64^3 box of the 512^3 D3Q19x3 workload (same parameters, one seed), FP64, OpenMP over z; "
+                    "%d samples, %d oracle steps in %.1f s, median rate" % (args.steps, total_steps, total_s)}
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 512 ** 3 / (value * 1e9) * 1e3,  # one 512^3 step at the sampled rate
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "kh512_q19x3 (bounded CPU sample: 64^3 box per step)",
                    "grid": [512, 512, 512], "lattices": [19, 19, 19]},
@@ -237,7 +255,7 @@ def run_own(args):
     # device->host read of the step's diagnostics (FP64 sums), final phi field read back to pinned memory
     e2e = None
     if rank == 0 or world > 1:
-        ke = max(2, args.steps // 2)
+        ke = max(2, min(50, args.steps // 2))
         phi_host = torch.empty(tuple(reversed(w.grid)), dtype=torch.float64, pin_memory=True).numpy()
         barrier_sync()
         t0 = time.perf_counter()
@@ -352,8 +370,8 @@ def run_variants(args, st):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--n", type=int, default=512, help="grid edge (the workload is defined at 512)")
     ap.add_argument("--workload", default="kh", choices=["kh", "pure2d"],
