@@ -193,28 +193,29 @@ __global__ void k_unpack(SimDev sd, int field, int par, LatRT L, int i, double* 
   }
 }
 
-// FP64 partial sums per block: [sum phi, sum U, sum theta, sum zeta(phi)(1+(1-k)U)].
+// FP64 partial sums per block: [sum phi, sum U, sum theta, sum phi U].
 template <typename T>
 __global__ void k_sums(const T* __restrict__ phi, const T* __restrict__ U, const T* __restrict__ th, double theta0,
                        double k, long long n, double* __restrict__ part) {
-  double a = 0, b = 0, c = 0, d = 0;
+  // sum phi, sum U, sum theta and sum phi U; the total solute follows from them (k_sums_final)
+  double a = 0, b = 0, c = 0, e = 0;
   for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
     const double p = (double)phi[s], u = (double)U[s];
     a += p;
     b += u;
-    c += th ? (double)th[s] : theta0;
-    d += 0.5 * ((1.0 + k) - (1.0 - k) * p) * (1.0 + (1.0 - k) * u);
+    if (th) c += (double)th[s];
+    e = fma(p, u, e);
   }
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_down_sync(0xffffffffu, a, o);
     b += __shfl_down_sync(0xffffffffu, b, o);
     c += __shfl_down_sync(0xffffffffu, c, o);
-    d += __shfl_down_sync(0xffffffffu, d, o);
+    e += __shfl_down_sync(0xffffffffu, e, o);
   }
   __shared__ double red[32][4];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) {
-    red[wid][0] = a; red[wid][1] = b; red[wid][2] = c; red[wid][3] = d;
+    red[wid][0] = a; red[wid][1] = b; red[wid][2] = c; red[wid][3] = e;
   }
   __syncthreads();
   if (threadIdx.x < 4) {
@@ -224,12 +225,25 @@ __global__ void k_sums(const T* __restrict__ phi, const T* __restrict__ U, const
   }
 }
 
-// Sum the per-block partials in a fixed order (deterministic).
-static __global__ void k_sums_final(const double* __restrict__ part, int nblk, double* __restrict__ out) {
+// Sum the per-block partials in a fixed order (deterministic).  The total solute
+// sum zeta(phi) (1 + (1-k) U), zeta = ((1+k) - (1-k) phi)/2, expands to
+// ((1+k) n + (1-k^2) sum U - (1-k) sum phi - (1-k)^2 sum phi U) / 2; theta frozen at
+// theta0 sums to n theta0.
+static __global__ void k_sums_final(const double* __restrict__ part, int nblk, double* __restrict__ out, double k,
+                                    long long n, int frozen_theta, double theta0) {
+  __shared__ double t4[4];
   if (threadIdx.x < 4) {
     double t = 0;
     for (int b = 0; b < nblk; ++b) t += part[b * 4 + threadIdx.x];
-    out[threadIdx.x] = t;
+    t4[threadIdx.x] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double dn = (double)n;
+    out[0] = t4[0];
+    out[1] = t4[1];
+    out[2] = frozen_theta ? dn * theta0 : t4[2];
+    out[3] = 0.5 * ((1.0 + k) * dn + (1.0 - k * k) * t4[1] - (1.0 - k) * t4[0] - (1.0 - k) * (1.0 - k) * t4[3]);
   }
 }
 

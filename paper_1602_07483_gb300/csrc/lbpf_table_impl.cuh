@@ -67,7 +67,7 @@ struct AuxImpl {
     k_sums<T><<<nblk, 256, 0, st>>>((const T*)phi, (const T*)U, (const T*)th, theta0, k, n, part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_sums_final<<<1, 32, 0, st>>>(part, nblk, part + 4 * nblk);
+    k_sums_final<<<1, 32, 0, st>>>(part, nblk, part + 4 * nblk, k, n, th == nullptr, theta0);
     return cudaGetLastError();
   }
   static cudaError_t tip(cudaStream_t st, const void* phi, int nx, int ny, int nz, int cx, int cy, int cz,
