@@ -59,7 +59,7 @@ def _velocity(series, dx, dt, window, end_step=None):
     return (end[1] - start[1]) * dx / ((end[0] - start[0]) * dt), (start[0], end[0])
 
 
-def precision(n=256, steps=8000, every=50, linf_at=200, window=1000, storages=("f64", "f32", "f16", "bf16")):
+def precision(n=256, steps=8000, every=50, linf_at=200, window=2000, storages=("f64", "f32", "f16", "bf16")):
     """The coupled heat + solute workload in several storage precisions.  The FP64 run
     stops once its tip nears the +x wall; the others then run exactly as many steps so
     that velocities and radii are compared over the same window."""
