@@ -179,6 +179,12 @@ int lbpf_destroy(lbpf_sim* sim);
 typedef struct lbpf_batch lbpf_batch;
 int lbpf_batch_create(int32_t n, lbpf_sim* const* sims, void* cuda_stream, lbpf_batch** out);
 int lbpf_batch_step(lbpf_batch* batch, int64_t n_steps);
+/* Tiling of the batched launches, as lbpf_set_tiling for one handle: `by` block
+ * rows (4..8, 0 keeps the current; ignored for 2D lattices, which use one-row
+ * blocks) and z-chunks of `zchunk` planes for every member (0: each member's
+ * default).  Results do not depend on the tiling.  LBPF_EINVAL for values out of
+ * range.  Synchronises the batch stream. */
+int lbpf_batch_set_tiling(lbpf_batch* batch, int32_t by, int32_t zchunk);
 int lbpf_batch_destroy(lbpf_batch* batch);
 
 /* Largest n_sites that lbpf_field_sums_noalloc accepts (65536 partial sums of

@@ -866,6 +866,36 @@ int lbpf_load(lbpf_sim* s, const char* path) {
 
 // ---------------------------------------------------------------- batch
 
+// Work items of all member simulations for blocks of `by` rows and z-chunks of
+// `zchunk` planes (0: each simulation's default), large chunks first.
+static int batch_tiling(lbpf_batch* b, int by, int zchunk) {
+  const KernelTable& t = *b->sims[0]->kt;
+  std::vector<WorkItem> items;
+  for (size_t i = 0; i < b->sims.size(); ++i) {
+    const lbpf_sim* s = b->sims[i];
+    const int zc = zchunk > 0 ? std::min(zchunk, s->kg.nz) : default_zchunk(s->kg.nx, s->kg.ny, s->kg.nz, by);
+    build_items((int)i, s->kg.nx, s->kg.ny, s->kg.nz, by, zc, items);
+  }
+  // interleave large and small simulations: sort items by descending z-chunk work
+  std::stable_sort(items.begin(), items.end(),
+                   [](const WorkItem& a, const WorkItem& c) { return (a.z1 - a.z0) > (c.z1 - c.z0); });
+  if (b->d_items) cudaFree(b->d_items);
+  b->d_items = nullptr;
+  if (cudaMalloc(&b->d_items, items.size() * sizeof(WorkItem)) != cudaSuccess ||
+      cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    return LBPF_ENOMEM;
+  }
+  b->nitems = (int)items.size();
+  b->by = by;
+  b->smem_phi = phi_smem_bytes(t, b->sims[0]->lat.q_phi, by);
+  b->smem_uth = uth_smem_bytes(t, b->sims[0]->lat.q_u, b->sims[0]->lat.q_theta, by);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  b->gexec = nullptr;
+  b->graph_ok = false;
+  return LBPF_OK;
+}
+
 int lbpf_batch_create(int32_t n, lbpf_sim* const* sims, void* cuda_stream, lbpf_batch** out) {
   if (!out || n < 1 || !sims) return LBPF_EINVAL;
   *out = nullptr;
@@ -880,28 +910,18 @@ int lbpf_batch_create(int32_t n, lbpf_sim* const* sims, void* cuda_stream, lbpf_
   b->sims.assign(sims, sims + n);
   b->stream = cuda_stream ? (cudaStream_t)cuda_stream : sims[0]->stream;
   const KernelTable& t = *sims[0]->kt;
-  b->by = lattice_is_2d(sims[0]->lat.q_phi) ? 1 : MAX_BLOCK_ROWS;
-  std::vector<WorkItem> items;
   std::vector<SimDev> descs;
   for (int i = 0; i < n; ++i) {
     lbpf_sim* s = sims[i];
     cudaStreamSynchronize(s->stream);
     fill_dev(s);
     descs.push_back(s->hd);
-    build_items(i, s->kg.nx, s->kg.ny, s->kg.nz, b->by, default_zchunk(s->kg.nx, s->kg.ny, s->kg.nz, b->by), items);
   }
-  // interleave large and small simulations: sort items by descending z-chunk work
-  std::stable_sort(items.begin(), items.end(),
-                   [](const WorkItem& a, const WorkItem& c) { return (a.z1 - a.z0) > (c.z1 - c.z0); });
-  b->nitems = (int)items.size();
   b->fphi = sims[0]->fphi;
   b->futh = sims[0]->futh;
-  b->smem_phi = phi_smem_bytes(t, sims[0]->lat.q_phi, b->by);
-  b->smem_uth = uth_smem_bytes(t, sims[0]->lat.q_u, sims[0]->lat.q_theta, b->by);
-  bool ok = cudaMalloc(&b->dd, descs.size() * sizeof(SimDev)) == cudaSuccess &&
-            cudaMalloc(&b->d_items, items.size() * sizeof(WorkItem)) == cudaSuccess;
+  bool ok = cudaMalloc(&b->dd, descs.size() * sizeof(SimDev)) == cudaSuccess;
   ok = ok && cudaMemcpy(b->dd, descs.data(), descs.size() * sizeof(SimDev), cudaMemcpyHostToDevice) == cudaSuccess;
-  ok = ok && cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && batch_tiling(b, lattice_is_2d(sims[0]->lat.q_phi) ? 1 : MAX_BLOCK_ROWS, 0) == LBPF_OK;
   const int a = q_index(sims[0]->lat.q_phi), qb = q_index(sims[0]->lat.q_u), qc = qt_index(sims[0]->lat.q_theta);
   ok = ok && raise_smem_limit(t.phi_fn[a], sims[0]->device) == LBPF_OK;
   ok = ok && raise_smem_limit(t.uth_fn[qb][qc], sims[0]->device) == LBPF_OK;
@@ -944,6 +964,15 @@ int lbpf_batch_step(lbpf_batch* b, int64_t n) {
   }
   for (lbpf_sim* s : b->sims) s->steps = steps;
   return LBPF_OK;
+}
+
+int lbpf_batch_set_tiling(lbpf_batch* b, int32_t by, int32_t zchunk) {
+  if (!b || by < 0 || zchunk < 0 || (by && (by < 4 || by > MAX_BLOCK_ROWS))) return LBPF_EINVAL;
+  for (lbpf_sim* s : b->sims)
+    if (s->sticky) return s->sticky;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return LBPF_ECUDA;
+  if (lattice_is_2d(b->sims[0]->lat.q_phi)) by = 1;  // 2D: one-row blocks
+  return batch_tiling(b, by ? by : b->by, zchunk);
 }
 
 int lbpf_batch_destroy(lbpf_batch* b) {

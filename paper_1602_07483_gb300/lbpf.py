@@ -87,6 +87,7 @@ def load(path: str = LIB_PATH):
             "lbpf_destroy": ([_VP], ctypes.c_int),
             "lbpf_batch_create": ([i32, ctypes.POINTER(_VP), _VP, ctypes.POINTER(_VP)], ctypes.c_int),
             "lbpf_batch_step": ([_VP, i64], ctypes.c_int),
+            "lbpf_batch_set_tiling": ([_VP, i32, i32], ctypes.c_int),
             "lbpf_batch_destroy": ([_VP], ctypes.c_int),
             "lbpf_strerror": ([ctypes.c_int], ctypes.c_char_p),
         }
@@ -233,6 +234,9 @@ class Batch:
 
     def step(self, n=1):
         _check(self._L.lbpf_batch_step(self._h, int(n)), "lbpf_batch_step")
+
+    def set_tiling(self, by=0, zchunk=0):
+        _check(self._L.lbpf_batch_set_tiling(self._h, int(by), int(zchunk)), "lbpf_batch_set_tiling")
 
     def close(self):
         if getattr(self, "_h", None):

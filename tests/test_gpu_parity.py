@@ -214,19 +214,37 @@ def test_tiling_does_not_change_results(storage):
         assert np.array_equal(x, y)
 
 
-def test_batch_matches_single_bitwise():
+@pytest.mark.parametrize("tiling", [(0, 0), (6, 16), (4, 8)])
+def test_batch_matches_single_bitwise(tiling):
+    """A batch (under its default tiling and two others set with lbpf_batch_set_tiling)
+    advances each member exactly as the member would alone."""
     sims = workloads.batch_sweep(count=4, storage="f32")
     singles = [lbpf.sim_from_workload(w) for w in sims]
     members = [lbpf.sim_from_workload(w) for w in sims]
     batch = lbpf.Batch(members)
+    if tiling != (0, 0):
+        batch.step(3)
+        batch.set_tiling(*tiling)
+        batch.step(11)
+    else:
+        batch.step(14)
     for s in singles:
         s.step(14)
-    batch.step(14)
     batch.close()
     for s, m in zip(singles, members):
         assert m.steps_done == 14
         for x, y in zip(s.read_fields(), m.read_fields()):
             assert np.array_equal(x, y)
+
+
+def test_batch_set_tiling_rejects_bad_values():
+    members = [lbpf.sim_from_workload(w) for w in workloads.batch_sweep(count=2, storage="f32")]
+    batch = lbpf.Batch(members)
+    with pytest.raises(lbpf.LbpfError):
+        batch.set_tiling(3, 0)
+    with pytest.raises(lbpf.LbpfError):
+        batch.set_tiling(9, 0)
+    batch.close()
 
 
 @pytest.mark.parametrize("storage", ["f64", "f32"])
