@@ -138,12 +138,29 @@ class OracleSample:
 
 
 def oracle_rate(budget_s=12.0, edge=64, threads=None):
-    """FP64 oracle site-updates/s on a bounded sample of the workload (see OracleSample)."""
+    """FP64 oracle site-updates/s on a bounded sample of the workload (see OracleSample), on all
+    host cores in this process and on one thread in a child process."""
     rate, steps, el = OracleSample(edge).rate(budget_s)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    one = oracle_rate_one_thread(budget_s=max(2.0, budget_s / 2), edge=32)
     return rate / 1e9, {"value": rate / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
                         "sample": "%d^3 box of the 512^3 D3Q19x3 workload (same parameters, one seed), "
-                                  "%d steps in %.1f s, FP64, OpenMP over z" % (edge, steps, el)}
+                                  "%d steps in %.1f s, FP64, OpenMP over z" % (edge, steps, el),
+                        "single_thread": one}
+
+
+def oracle_rate_one_thread(budget_s=6.0, edge=32):
+    """The same oracle sample on one host thread (OMP_NUM_THREADS=1 in a child process)."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "r, n, el = bench.OracleSample(%d).rate(%r); print(json.dumps([r, n, el]))" % (ROOT, edge, budget_s))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+        r, n, el = json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as e:  # the CPU leg must not hide the GPU result
+        return {"value": None, "cores": 1, "sample": "failed: %s" % e}
+    return {"value": r / 1e9, "unit": UNIT, "cores": 1,
+            "sample": "%d^3 box, %d steps in %.1f s, FP64, one thread" % (edge, n, el)}
 
 
 def run_reference(args):
@@ -172,10 +189,11 @@ def run_reference(args):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 512 ** 3 / (value * 1e9) * 1e3,  # one 512^3 step at the sampled rate
+        "ms_per_step": 64 ** 3 / (value * 1e9) * 1e3,  # one step of the sampled 64^3 box, measured
+        "implied_ms_per_step_512": 512 ** 3 / (value * 1e9) * 1e3,  # a 512^3 step at the sampled rate
         "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "kh512_q19x3 (bounded CPU sample: 64^3 box per step)",
+        "config": {"workload": "kh512_q19x3 (bounded CPU sample: each step is one step of a 64^3 box of it)",
                    "grid": [512, 512, 512], "lattices": [19, 19, 19]},
         "cpu_baseline": cb,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -226,6 +244,16 @@ def run_own(args):
     ms_phi, ms_uth, ms_span = sim.step_timed(args.steps)
     barrier_sync()
     clk = clocks.stop()
+    developed = None
+    if args.developed and rank == 0 and world == 1 and args.workload == "kh":
+        # the same simulation after it has grown for `developed` steps from the seeds
+        sim.step(max(0, args.developed - args.warmup - args.steps))
+        dk = 50
+        d_phi, d_uth, d_span = sim.step_timed(dk)
+        developed = {"after_steps": sim.steps_done - dk, "steps": dk, "GLUPS": w.sites * dk / (d_span * 1e-3) / 1e9,
+                     "phi_ms": d_phi / dk, "uth_ms": d_uth / dk,
+                     "what": "the timed simulation advanced to step %d, then %d steps timed as above" % (
+                         sim.steps_done - dk, dk)}
     sites = w.sites
     rate, t_max, _ = job_rate(ms_span / 1e3, sites * args.steps)
     value = rate / 1e9
@@ -312,6 +340,7 @@ def run_own(args):
             "e2e": e2e,
             "gpu_launches": 2 * args.steps,
             "clocks": clk,
+            "developed": developed,
             "variants": variants,
         }
         print(json.dumps(line), flush=True)
@@ -329,23 +358,37 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+def _timed(s, k):
+    """Per-kernel and whole-step device times of k steps of a simulation (ms per step)."""
+    ms_phi, ms_uth, span = s.step_timed(k)
+    return ms_phi / k, ms_uth / k, span / k
+
+
 def run_variants(args, st):
-    """FP16-storage form at 512^3 and the plain FP64 form at 256^3 (same workload recipe),
-    and the 2D scheme in FP32 on 8192^2."""
+    """The FP16-storage form at 512^3, the plain FP64 form at 256^3, the same 512^3 workload
+    with interface at most sites, the 2D scheme in FP32 on 8192^2, and the batched FP16
+    sweep of 64 uneven simulations against the same simulations one by one in FP64."""
     import torch
     from paper_1602_07483_gb300 import lbpf, workloads
+    hbm, _ = measured_peaks()
     out = {}
-    for storage, n, k in (("f16", args.n, 10), ("f64", 256, 6)):
-        w = workloads.large_kh(n)
+    for name, w, storage, k in (("f16", workloads.large_kh(args.n), "f16", 10),
+                                ("f64", workloads.large_kh(256), "f64", 6),
+                                ("dense_interface_f32", workloads.dense_kh(args.n), "f32", 10)):
         s = lbpf.Sim(w.grid, w.lattices, storage=storage, stream=st.cuda_stream, **w.params)
         s.init_seed(w.centres, w.radii, w.U0, w.theta0)
         s.step(3)
         torch.cuda.synchronize()
-        ms_phi, ms_uth, span = s.step_timed(k)
-        sb = {"f16": 2, "f64": 8}[storage]
-        glups = w.sites * k / (span * 1e-3) / 1e9
-        out[storage] = {"grid": n, "GLUPS": glups, "ms_per_step": span / k,
-                        "alg_GBps": glups * 2 * sb * 57, "bound": "hbm" if storage != "f64" else "alu (FP64 rate)"}
+        phi_ms, uth_ms, ms = _timed(s, k)
+        sb = {"f16": 2, "f32": 4, "f64": 8}[storage]
+        glups = w.sites / (ms * 1e-3) / 1e9
+        alg = glups * 2 * sb * 57
+        out[name] = {"grid": list(w.grid), "storage": storage, "GLUPS": glups, "ms_per_step": ms,
+                     "phi_ms": phi_ms, "uth_ms": uth_ms, "alg_GBps": alg, "hbm_frac": alg / hbm}
+        if name == "f64":
+            out[name]["fp64_GFLOPs"] = glups * 687  # FP64 operations per site-update counted by ncu (halo included)
+        if name.startswith("dense"):
+            out[name]["seeds"] = len(w.radii)
         s.close()
         del s
         torch.cuda.empty_cache()
@@ -355,16 +398,58 @@ def run_variants(args, st):
     s.init_seed(w.centres, w.radii, w.U0, w.theta0)
     s.step(3)
     torch.cuda.synchronize()
-    k = 10
-    ms_phi, ms_uth, span = s.step_timed(k)
-    glups = w.sites * k / (span * 1e-3) / 1e9
+    phi_ms, uth_ms, ms = _timed(s, 10)
+    glups = w.sites / (ms * 1e-3) / 1e9
     alg = glups * 2 * 4 * sum(w.lattices)
-    out["pure2d_f32"] = {"grid": [8192, 8192, 1], "lattices": list(w.lattices), "GLUPS": glups, "ms_per_step": span / k,
-                         "alg_GBps": alg, "bound": "hbm", "phi_ms": ms_phi / k, "uth_ms": ms_uth / k}
+    out["pure2d_f32"] = {"grid": [8192, 8192, 1], "lattices": list(w.lattices), "GLUPS": glups, "ms_per_step": ms,
+                         "alg_GBps": alg, "hbm_frac": alg / hbm, "phi_ms": phi_ms, "uth_ms": uth_ms}
     s.close()
     del s
     torch.cuda.empty_cache()
+    out["sweep_f16"] = run_sweep(st, hbm)
     return out
+
+
+def run_sweep(st, hbm, steps=60, base_steps=12):
+    """The batched parameter sweep: 64 simulations with edges from {48, 64, 80, 96}, Delta, eps
+    and k drawn by default_rng(11), FP16 storage, advanced together by one library-owned batch
+    (graph-replayed steps, CUDA events on the batch stream); then the same simulations one by one
+    in plain FP64.  Algorithmic bytes: 2 x 2 B x 38 populations = 152 B per FP16 site-update."""
+    import numpy as np
+    import torch
+    from paper_1602_07483_gb300 import lbpf, workloads
+    ws = workloads.batch_sweep(count=64, storage="f16")
+    sites = sum(w.sites for w in ws)
+    b = lbpf.batch_from_workloads(ws, stream=st.cuda_stream)
+    b.step(6)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    b.step(steps)
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    nonfinite = [i for i, m in enumerate(b.sims) if not np.all(np.isfinite(m.sums(check=False)))]
+    b.close()
+    del b
+    glups = sites * steps / (ms * 1e-3) / 1e9
+    t_one = 0.0
+    for w in ws:
+        s = lbpf.Sim(w.grid, w.lattices, storage="f64", stream=st.cuda_stream, **w.params)
+        s.init_seed(w.centres, w.radii, w.U0, w.theta0)
+        s.step(6)
+        torch.cuda.synchronize()
+        e0.record(st)
+        s.step(base_steps)
+        e1.record(st)
+        e1.synchronize()
+        t_one += e0.elapsed_time(e1)
+        s.close()
+    torch.cuda.empty_cache()
+    base = sites * base_steps / (t_one * 1e-3) / 1e9
+    return {"sims": len(ws), "sites": sites, "steps": steps, "storage": "f16", "GLUPS": glups,
+            "alg_GBps": glups * 152, "hbm_frac": glups * 152 / hbm, "one_by_one_f64_GLUPS": base,
+            "one_by_one_f64_steps": base_steps, "speedup": glups / base, "nonfinite_sims": nonfinite}
 
 
 def main():
@@ -381,6 +466,8 @@ def main():
                     help="population storage (the headline line is f32)")
     ap.add_argument("--autotune", type=int, default=0)
     ap.add_argument("--variants", type=int, default=1)
+    ap.add_argument("--developed", type=int, default=2000,
+                    help="also time the headline simulation after it has run this many steps (0: skip)")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -47,8 +47,7 @@ extern "C" {
 #define LBPF_EUNSTABLE (-2) /* parameters give a relaxation time <= 1/2 somewhere */
 #define LBPF_ENOMEM (-3)    /* device allocation failed */
 #define LBPF_ENAN (-4)      /* a non-finite value was found in the fields */
-#define LBPF_ETIMEOUT (-5)  /* a bounded device wait gave up */
-#define LBPF_ECUDA (-6)     /* CUDA runtime error (sticky) */
+#define LBPF_ECUDA (-6)     /* CUDA runtime error (sticky); -5 is not used */
 
 /* storage of the distributions; arithmetic is FP64 for LBPF_F64, FP32 otherwise */
 #define LBPF_F64 0
@@ -140,13 +139,18 @@ int lbpf_read_fields(lbpf_sim* sim, uint32_t mask, double* phi, double* U, doubl
  * Returns LBPF_ENAN (after filling out) when any sum is not finite.  Synchronous. */
 int lbpf_sums(lbpf_sim* sim, double out[4]);
 
-/* Dendrite tip along +x from node `centre` (3 ints): the first crossing
- * phi_i >= 0 > phi_{i+1}, linearly interpolated, in lattice units (-1 when none).
- * rho (may be NULL): tip radius in lattice units from a least-squares parabola
- * x(j) = x_tip - j^2 / (2 rho) through the crossings of rows j = +-1..+-4 in the
- * xy and xz planes through the centre, averaged; on an nz = 1 grid the xy plane
- * alone (-1 when undefined).  Synchronous. */
-int lbpf_tip(lbpf_sim* sim, const int32_t centre[3], double* x_tip, double* rho);
+/* Dendrite tip and tip radius (the tip velocity of Sec. 4.1 is the tip's displacement per
+ * unit time).  axis: 0, 1, 2 = scan along +x, +y, +z (0 or 1 on a 2D grid).  centre_lu:
+ * 3 lattice coordinates (x, y, z; z ignored on a 2D grid, give 0); the scan starts at the
+ * node nearest to them, which must lie in the grid.  x_tip_lu: the first crossing
+ * phi_i >= 0 > phi_{i+1} along the axis from that node, linearly interpolated, as a
+ * coordinate along the axis in lattice units (-1 when none).  rho_lu (may be NULL): tip
+ * radius in lattice units, a least-squares parabola t(j) = t_tip - j^2 / (2 rho) through
+ * the crossings of the lines offset by j = +-1..+-4 along each other axis, one fit per
+ * plane spanned by the scan axis and an axis with more than one node, averaged (the two
+ * planes in 3D, the grid plane on a 2D or nz = 1 grid; -1 when undefined).
+ * LBPF_EINVAL for a bad axis or a centre outside the grid.  Synchronous. */
+int lbpf_tip(lbpf_sim* sim, int32_t axis, const double centre_lu[3], double* x_tip_lu, double* rho_lu);
 
 /* Number of steps taken since the last init / set_state / load. */
 int64_t lbpf_steps_done(const lbpf_sim* sim);
@@ -172,12 +176,30 @@ int lbpf_autotune(lbpf_sim* sim, int32_t steps, double* best_ms);
 
 int lbpf_destroy(lbpf_sim* sim);
 
-/* Batched stepping: `n` handles created with identical lattices and storage
- * (grids and physical parameters may differ) advance together, one launch per
- * kernel phase covering the tiles of all simulations, captured in one CUDA
- * graph.  The batch borrows the handles; destroy the batch before them. */
+/* Batched stepping: several independent simulations with identical lattices and storage
+ * (grids and physical parameters may differ, e.g. the parameter sweeps over Delta, eps
+ * and k of the paper's Sec. 4 studies) advance together, one launch per kernel phase
+ * covering the tiles of all members, with the time loop captured in one CUDA graph.
+ *
+ * lbpf_batch_create: creates n member simulations, member i from grids[i], lattices[i]
+ * and params[i] as lbpf_create would (all lattices[i] equal, all params[i].storage equal,
+ * else LBPF_EINVAL; a failing member's lbpf_create code is returned).  The batch owns the
+ * members and destroys them in lbpf_batch_destroy.  All members run on `cuda_stream`
+ * (borrowed), or on a non-blocking stream the batch owns when it is NULL.  Get a member's
+ * handle with lbpf_batch_member to seed it, read it or step it alone. */
 typedef struct lbpf_batch lbpf_batch;
-int lbpf_batch_create(int32_t n, lbpf_sim* const* sims, void* cuda_stream, lbpf_batch** out);
+int lbpf_batch_create(int32_t n, const lbpf_grid* grids, const lbpf_lattice* lattices, const lbpf_params* params,
+                      void* cuda_stream, lbpf_batch** out);
+/* The i-th member of a batch (0 <= i < n); the handle stays owned by whoever created it. */
+int lbpf_batch_member(const lbpf_batch* batch, int32_t i, lbpf_sim** out);
+/* A batch over handles the caller already created (they stay the caller's; destroy the
+ * batch before them).  The batch runs on `cuda_stream`, or on the first member's stream
+ * when NULL; lbpf_batch_step orders itself after the work each member has enqueued on its
+ * own stream and makes each member's stream wait for the batch's work, so calls on a
+ * member between batch steps need no extra synchronisation. */
+int lbpf_batch_from_sims(int32_t n, lbpf_sim* const* sims, void* cuda_stream, lbpf_batch** out);
+/* Enqueue n_steps steps of every member (asynchronous).  All members must have taken the
+ * same number of steps (LBPF_EINVAL otherwise). */
 int lbpf_batch_step(lbpf_batch* batch, int64_t n_steps);
 /* Tiling of the batched launches, as lbpf_set_tiling for one handle: `by` block
  * rows (4..8, 0 keeps the current; ignored for 2D lattices, which use one-row
@@ -193,23 +215,24 @@ int lbpf_batch_destroy(lbpf_batch* batch);
 
 /* The same four FP64 sums as lbpf_sums, over caller-owned DEVICE arrays, with
  * no memory allocation at all.  The paper has no counterpart: this serves
- * callers that hold device fields but cannot call cudaMalloc -- code running
- * while a stream is captured (allocation is not allowed there), loops that
- * must avoid the implicit device synchronisation of cudaMalloc/cudaFree, and
- * hosts whose device memory is fully reserved by another allocator.
+ * callers that hold device fields but cannot call cudaMalloc -- loops that must
+ * avoid the implicit device synchronisation of cudaMalloc/cudaFree, and hosts
+ * whose device memory is fully reserved by another allocator.
  *   phi, U, theta: device arrays of n_sites elements of the compute type of
  *     `storage` (double for LBPF_F64, float otherwise); theta may be NULL, then
  *     theta0 is used at every site.
  *   k: partition coefficient of the solute sum.  out: HOST array of 4 doubles.
  *   cuda_stream: stream to run on (NULL = legacy default stream); the call
- *     synchronises it before returning.
+ *     copies the sums to `out` and synchronises the stream before returning, so
+ *     a stream that is being captured is refused (LBPF_EINVAL, nothing enqueued).
  * The reduction scratch (2 MiB) is a file-scope device array that every GPU
  * loading the library keeps until the process exits; all calls on a device
  * share it and each call overwrites the part it uses, so nothing in it needs
  * clearing.  Calls that overlap on the GPU (several streams or host threads at
  * once) race on that scratch and must be serialised by the caller.  The first
  * call on a device looks up the scratch's device address with
- * cudaGetSymbolAddress; make that first call before any stream capture.
+ * cudaGetSymbolAddress and keeps it for the process; make that first call before
+ * any stream capture, and do not call again on a device after cudaDeviceReset.
  * Returns LBPF_EINVAL for NULL inputs, n_sites < 1 or
  * n_sites > LBPF_NOALLOC_MAX_SITES, LBPF_ENAN when a sum is not finite,
  * LBPF_ECUDA on a CUDA error. */

@@ -99,7 +99,7 @@ def load(openmp: bool = True):
         L.ora_get_usource.argtypes = [vp, _D]
         L.ora_step.argtypes = [vp, ctypes.c_int64]
         L.ora_sums.argtypes = [vp, _D]
-        L.ora_tip.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
+        L.ora_tip.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]
         L.ora_tip.restype = ctypes.c_double
         L.ora_steps_done.argtypes = [vp]
         L.ora_steps_done.restype = ctypes.c_int64
@@ -211,9 +211,10 @@ class Sim:
         self._L.ora_sums(self._h, _ptr(out))
         return out
 
-    def tip(self, c):
+    def tip(self, c, axis=0):
+        """Tip coordinate along +axis from node c and the tip radius (see ora_tip)."""
         rho = np.zeros(1)
-        x = self._L.ora_tip(self._h, int(c[0]), int(c[1]), int(c[2]), _ptr(rho))
+        x = self._L.ora_tip(self._h, int(axis), int(c[0]), int(c[1]), int(c[2]), _ptr(rho))
         return x, float(rho[0])
 
     @property

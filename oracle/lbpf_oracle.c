@@ -533,38 +533,52 @@ void ora_sums(const ora_sim* s, double out[4]) {
   out[0] = a; out[1] = b; out[2] = c; out[3] = d;
 }
 
-/* first crossing phi_i >= 0 > phi_{i+1} scanning +x from column x0 on row (y, z) */
-static double crossing_x(const ora_sim* s, int x0, int y, int z) {
-  if (y < 0 || z < 0 || y >= s->ny || z >= s->nz) return -1.0;
-  for (int x = x0; x + 1 < s->nx; ++x) {
-    const double a = s->phi[IDX(s, x, y, z)], b = s->phi[IDX(s, x + 1, y, z)];
-    if (a >= 0.0 && b < 0.0) return x + a / (a - b);
+/* first crossing phi_i >= 0 > phi_{i+1} scanning +axis from node p0 along its line */
+static double crossing(const ora_sim* s, int axis, const int p0[3]) {
+  const int n[3] = {s->nx, s->ny, s->nz};
+  for (int a = 0; a < 3; ++a)
+    if (p0[a] < 0 || p0[a] >= n[a]) return -1.0;
+  int p[3] = {p0[0], p0[1], p0[2]};
+  int q[3] = {p0[0], p0[1], p0[2]};
+  for (int t = p0[axis]; t + 1 < n[axis]; ++t) {
+    p[axis] = t;
+    q[axis] = t + 1;
+    const double a = s->phi[IDX(s, p[0], p[1], p[2])], b = s->phi[IDX(s, q[0], q[1], q[2])];
+    if (a >= 0.0 && b < 0.0) return t + a / (a - b);
   }
   return -1.0;
 }
 
-double ora_tip(const ora_sim* s, int cx, int cy, int cz, double* rho) {
-  const double xt = crossing_x(s, cx, cy, cz);
+/* Tip along +axis from node c (Sec. 4.1 tip reading): x_tip is the first crossing on the
+ * line through c; rho is the least-squares parabola x(j) = x_tip - j^2/(2 rho) through the
+ * crossings of the lines offset by j = +-1..+-4 along each other axis b, one fit per plane
+ * (axis, b), averaged over the planes that exist (extent along b > 1: both in 3D, the
+ * grid plane on an nz = 1 grid). */
+double ora_tip(const ora_sim* s, int axis, int cx, int cy, int cz, double* rho) {
+  const int c[3] = {cx, cy, cz};
+  const int n[3] = {s->nx, s->ny, s->nz};
+  const double xt = crossing(s, axis, c);
   if (rho) {
-    /* parabola x(j) = x_tip - j^2/(2 rho), least squares in u = 1/(2 rho),
-     * rows j = +-1..+-4 in the z = cz plane and in the y = cy plane */
-    double r[2] = {-1.0, -1.0};
-    for (int plane = 0; plane < 2; ++plane) {
-      double num = 0.0, den = 0.0;
-      int ok = 1;
+    double sum = 0.0;
+    int planes = 0, ok_all = 1;
+    for (int b = 0; b < 3; ++b) {
+      if (b == axis || n[b] == 1) continue;
+      double num = 0.0, den = 0.0; /* least squares in u = 1/(2 rho): u = num / den */
+      int ok = xt >= 0.0;
       for (int j = -4; j <= 4; ++j) {
         if (j == 0) continue;
-        const double xj = plane == 0 ? crossing_x(s, cx, cy + j, cz) : crossing_x(s, cx, cy, cz + j);
-        if (xj < 0.0 || xt < 0.0) { ok = 0; break; }
+        int p[3] = {cx, cy, cz};
+        p[b] += j;
+        const double xj = crossing(s, axis, p);
+        if (xj < 0.0) ok = 0;
         num += (double)(j * j) * (xt - xj);
         den += (double)(j * j) * (double)(j * j);
       }
-      if (ok && num > 0.0) r[plane] = den / (2.0 * num); /* u = num/den, rho = 1/(2u) */
+      if (ok && num > 0.0) sum += den / (2.0 * num);
+      else ok_all = 0;
+      ++planes;
     }
-    if (s->nz == 1) /* 2D grid: the xy plane only */
-      *rho = r[0] > 0.0 ? r[0] : -1.0;
-    else
-      *rho = (r[0] > 0.0 && r[1] > 0.0) ? 0.5 * (r[0] + r[1]) : -1.0;
+    *rho = (planes > 0 && ok_all) ? sum / planes : -1.0;
   }
   return xt;
 }

@@ -72,11 +72,12 @@ void ora_get_usource(const ora_sim* s, double* out);
 
 /* Diagnostics.  Sums: [sum phi, sum U, sum theta, sum zeta(phi)(1+(1-k)U)]. */
 void ora_sums(const ora_sim* s, double out[4]);
-/* Tip along +x from node (cx, cy, cz): first crossing phi>=0>phi_next, linear
- * interpolation.  Returns x_tip (lattice units) or -1 when no crossing.
- * rho (may be NULL): tip radius in lattice units from the parabola fit (xy and xz
- * planes averaged; the xy plane alone on an nz = 1 grid). */
-double ora_tip(const ora_sim* s, int cx, int cy, int cz, double* rho);
+/* Tip along +axis (0, 1, 2 = x, y, z) from node (cx, cy, cz): first crossing
+ * phi >= 0 > phi_next, linear interpolation.  Returns the tip coordinate along the axis
+ * (lattice units) or -1 when there is no crossing.  rho (may be NULL): tip radius in
+ * lattice units from the parabola fit in each plane spanned by the axis and another axis
+ * with more than one node, averaged (-1 when undefined). */
+double ora_tip(const ora_sim* s, int axis, int cx, int cy, int cz, double* rho);
 
 int64_t ora_steps_done(const ora_sim* s);
 

@@ -113,7 +113,11 @@ struct lbpf_sim {
 
 struct lbpf_batch {
   std::vector<lbpf_sim*> sims;
+  bool owns_sims = false;       // members created by lbpf_batch_create (destroyed with the batch)
   cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaEvent_t ev = nullptr;     // orders the batch stream against the members' own streams
+  SimDev* h_desc = nullptr;     // pinned copy of the member descriptors last uploaded to dd
   SimDev* dd = nullptr;
   WorkItem* d_items = nullptr;
   int nitems = 0;
@@ -354,7 +358,6 @@ const char* lbpf_strerror(int code) {
     case LBPF_EUNSTABLE: return "unstable parameters: a relaxation time a_s^2 eta <= 1/2";
     case LBPF_ENOMEM: return "device allocation failed";
     case LBPF_ENAN: return "non-finite value in the fields";
-    case LBPF_ETIMEOUT: return "bounded device wait timed out";
     case LBPF_ECUDA: return "CUDA runtime error";
     default: return "unknown error";
   }
@@ -583,15 +586,24 @@ int lbpf_sums(lbpf_sim* s, double out[4]) {
   return fin ? LBPF_OK : LBPF_ENAN;
 }
 
-int lbpf_tip(lbpf_sim* s, const int32_t centre[3], double* x_tip, double* rho) {
-  if (!s || !centre || !x_tip) return LBPF_EINVAL;
+int lbpf_tip(lbpf_sim* s, int32_t axis, const double centre_lu[3], double* x_tip, double* rho) {
+  if (!s || !centre_lu || !x_tip) return LBPF_EINVAL;
   if (s->sticky) return s->sticky;
-  // radius planes: both (xy, xz); the xy plane alone on an nz = 1 grid, which for the 2D
-  // lattices is the kernel's xz plane
   const bool d2 = lattice_is_2d(s->lat.q_phi);
-  const int planes = d2 ? 2 : (s->g.nz == 1 ? 1 : 0);
-  CK(s, s->kt->tip(s->stream, s->phi[s6_of(s) % 3], s->kg.nx, s->kg.ny, s->kg.nz, centre[0], d2 ? centre[2] : centre[1],
-                   d2 ? centre[1] : centre[2], planes, s->d_small));
+  if (axis < 0 || axis > (d2 ? 1 : 2)) return LBPF_EINVAL;
+  // the scan starts at the node nearest to the centre
+  int c[3];
+  const int n[3] = {s->g.nx, s->g.ny, s->g.nz};
+  for (int a = 0; a < 3; ++a) {
+    if (!isfinite(centre_lu[a])) return LBPF_EINVAL;
+    const double v = floor(centre_lu[a] + 0.5);
+    if (v < 0 || v >= n[a]) return LBPF_EINVAL;
+    c[a] = (int)v;
+  }
+  // kernel coordinates: a 2D grid (nx, ny, 1) runs as (nx, 1, ny), the paper's y on the kernel's z
+  const int kaxis = d2 && axis == 1 ? 2 : axis;
+  CK(s, s->kt->tip(s->stream, s->phi[s6_of(s) % 3], s->kg.nx, s->kg.ny, s->kg.nz, kaxis, c[0], d2 ? c[2] : c[1],
+                   d2 ? c[1] : c[2], s->d_small));
   CK(s, cudaMemcpyAsync(s->h_small, s->d_small, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   CK(s, cudaStreamSynchronize(s->stream));
   *x_tip = s->h_small[0];
@@ -896,41 +908,114 @@ static int batch_tiling(lbpf_batch* b, int by, int zchunk) {
   return LBPF_OK;
 }
 
-int lbpf_batch_create(int32_t n, lbpf_sim* const* sims, void* cuda_stream, lbpf_batch** out) {
-  if (!out || n < 1 || !sims) return LBPF_EINVAL;
-  *out = nullptr;
-  for (int i = 0; i < n; ++i) {
-    if (!sims[i]) return LBPF_EINVAL;
-    if (sims[i]->sticky) return sims[i]->sticky;
-    if (memcmp(&sims[i]->lat, &sims[0]->lat, sizeof(lbpf_lattice)) != 0 || sims[i]->p.storage != sims[0]->p.storage ||
-        sims[i]->device != sims[0]->device)
+namespace {
+// Shared set-up of both batch constructors: the members are in b->sims and b->stream is set.
+int batch_init(lbpf_batch* b) {
+  lbpf_sim* s0 = b->sims[0];
+  for (lbpf_sim* s : b->sims) {
+    if (!s) return LBPF_EINVAL;
+    if (s->sticky) return s->sticky;
+    if (memcmp(&s->lat, &s0->lat, sizeof(lbpf_lattice)) != 0 || s->p.storage != s0->p.storage || s->device != s0->device)
       return LBPF_EINVAL;
   }
+  const KernelTable& t = *s0->kt;
+  const size_t n = b->sims.size();
+  for (lbpf_sim* s : b->sims) cudaStreamSynchronize(s->stream);
+  b->fphi = s0->fphi;
+  b->futh = s0->futh;
+  bool ok = cudaMallocHost(&b->h_desc, n * sizeof(SimDev)) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->dd, n * sizeof(SimDev)) == cudaSuccess;
+  if (ok) {
+    for (size_t i = 0; i < n; ++i) {
+      fill_dev(b->sims[i]);
+      b->h_desc[i] = b->sims[i]->hd;
+    }
+  }
+  ok = ok && cudaMemcpy(b->dd, b->h_desc, n * sizeof(SimDev), cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && batch_tiling(b, lattice_is_2d(s0->lat.q_phi) ? 1 : MAX_BLOCK_ROWS, 0) == LBPF_OK;
+  const int a = q_index(s0->lat.q_phi), qb = q_index(s0->lat.q_u), qc = qt_index(s0->lat.q_theta);
+  ok = ok && raise_smem_limit(t.phi_fn[a], s0->device) == LBPF_OK;
+  ok = ok && raise_smem_limit(t.uth_fn[qb][qc], s0->device) == LBPF_OK;
+  if (!ok) {
+    cudaGetLastError();
+    return LBPF_ENOMEM;
+  }
+  return LBPF_OK;
+}
+
+// Re-upload the member descriptors when a member's state changed since the last upload
+// (for instance a new U0 or theta0 from lbpf_init_seed, which the FP16 codec shifts by).
+int batch_refresh(lbpf_batch* b) {
+  bool changed = false;
+  for (size_t i = 0; i < b->sims.size(); ++i) {
+    fill_dev(b->sims[i]);
+    changed = changed || memcmp(&b->sims[i]->hd, &b->h_desc[i], sizeof(SimDev)) != 0;
+  }
+  if (!changed) return LBPF_OK;
+  // the pinned buffer may still feed an earlier upload: let the stream drain first
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return LBPF_ECUDA;
+  for (size_t i = 0; i < b->sims.size(); ++i) b->h_desc[i] = b->sims[i]->hd;
+  if (cudaMemcpyAsync(b->dd, b->h_desc, b->sims.size() * sizeof(SimDev), cudaMemcpyHostToDevice, b->stream) !=
+      cudaSuccess)
+    return LBPF_ECUDA;
+  return LBPF_OK;
+}
+}  // namespace
+
+int lbpf_batch_from_sims(int32_t n, lbpf_sim* const* sims, void* cuda_stream, lbpf_batch** out) {
+  if (!out || n < 1 || !sims) return LBPF_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i)
+    if (!sims[i]) return LBPF_EINVAL;
   lbpf_batch* b = new lbpf_batch();
   b->sims.assign(sims, sims + n);
   b->stream = cuda_stream ? (cudaStream_t)cuda_stream : sims[0]->stream;
-  const KernelTable& t = *sims[0]->kt;
-  std::vector<SimDev> descs;
-  for (int i = 0; i < n; ++i) {
-    lbpf_sim* s = sims[i];
-    cudaStreamSynchronize(s->stream);
-    fill_dev(s);
-    descs.push_back(s->hd);
-  }
-  b->fphi = sims[0]->fphi;
-  b->futh = sims[0]->futh;
-  bool ok = cudaMalloc(&b->dd, descs.size() * sizeof(SimDev)) == cudaSuccess;
-  ok = ok && cudaMemcpy(b->dd, descs.data(), descs.size() * sizeof(SimDev), cudaMemcpyHostToDevice) == cudaSuccess;
-  ok = ok && batch_tiling(b, lattice_is_2d(sims[0]->lat.q_phi) ? 1 : MAX_BLOCK_ROWS, 0) == LBPF_OK;
-  const int a = q_index(sims[0]->lat.q_phi), qb = q_index(sims[0]->lat.q_u), qc = qt_index(sims[0]->lat.q_theta);
-  ok = ok && raise_smem_limit(t.phi_fn[a], sims[0]->device) == LBPF_OK;
-  ok = ok && raise_smem_limit(t.uth_fn[qb][qc], sims[0]->device) == LBPF_OK;
-  if (!ok) {
-    cudaGetLastError();
+  const int rc = batch_init(b);
+  if (rc != LBPF_OK) {
     lbpf_batch_destroy(b);
-    return LBPF_ENOMEM;
+    return rc;
   }
   *out = b;
+  return LBPF_OK;
+}
+
+int lbpf_batch_create(int32_t n, const lbpf_grid* grids, const lbpf_lattice* lattices, const lbpf_params* params,
+                      void* cuda_stream, lbpf_batch** out) {
+  if (!out || n < 1 || !grids || !lattices || !params) return LBPF_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i)
+    if (memcmp(&lattices[i], &lattices[0], sizeof(lbpf_lattice)) != 0 || params[i].storage != params[0].storage)
+      return LBPF_EINVAL;
+  lbpf_batch* b = new lbpf_batch();
+  b->owns_sims = true;
+  if (cuda_stream) {
+    b->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete b;
+      return LBPF_ECUDA;
+    }
+    b->own_stream = true;
+  }
+  int rc = LBPF_OK;
+  for (int i = 0; i < n && rc == LBPF_OK; ++i) {
+    lbpf_sim* s = nullptr;
+    rc = lbpf_create(&grids[i], &lattices[i], &params[i], b->stream, &s);
+    if (rc == LBPF_OK) b->sims.push_back(s);
+  }
+  if (rc == LBPF_OK) rc = batch_init(b);
+  if (rc != LBPF_OK) {
+    lbpf_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return LBPF_OK;
+}
+
+int lbpf_batch_member(const lbpf_batch* b, int32_t i, lbpf_sim** out) {
+  if (!b || !out || i < 0 || i >= (int32_t)b->sims.size()) return LBPF_EINVAL;
+  *out = b->sims[(size_t)i];
   return LBPF_OK;
 }
 
@@ -941,6 +1026,14 @@ int lbpf_batch_step(lbpf_batch* b, int64_t n) {
     if (s->sticky) return s->sticky;
     if (s->steps != st0) return LBPF_EINVAL;  // batch members advance in lockstep
   }
+  // work the members enqueued on their own streams comes first
+  for (lbpf_sim* s : b->sims)
+    if (s->stream != b->stream) {
+      if (cudaEventRecord(b->ev, s->stream) != cudaSuccess || cudaStreamWaitEvent(b->stream, b->ev, 0) != cudaSuccess)
+        return LBPF_ECUDA;
+    }
+  int rc = batch_refresh(b);
+  if (rc != LBPF_OK) return rc;
   int64_t steps = st0;
   while (n > 0) {
     const int s6 = (int)(steps % kGraphSteps);
@@ -963,6 +1056,10 @@ int lbpf_batch_step(lbpf_batch* b, int64_t n) {
     }
   }
   for (lbpf_sim* s : b->sims) s->steps = steps;
+  // later work on a member's own stream (reads, sums, single steps) waits for the batch
+  if (cudaEventRecord(b->ev, b->stream) != cudaSuccess) return LBPF_ECUDA;
+  for (lbpf_sim* s : b->sims)
+    if (s->stream != b->stream && cudaStreamWaitEvent(s->stream, b->ev, 0) != cudaSuccess) return LBPF_ECUDA;
   return LBPF_OK;
 }
 
@@ -980,7 +1077,12 @@ int lbpf_batch_destroy(lbpf_batch* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   if (b->dd) cudaFree(b->dd);
+  if (b->h_desc) cudaFreeHost(b->h_desc);
   if (b->d_items) cudaFree(b->d_items);
+  if (b->ev) cudaEventDestroy(b->ev);
+  if (b->owns_sims)
+    for (lbpf_sim* s : b->sims) lbpf_destroy(s);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
   delete b;
   return LBPF_OK;
 }

@@ -247,32 +247,35 @@ static __global__ void k_sums_final(const double* __restrict__ part, int nblk, d
   }
 }
 
-// Tip tracking.  Warp r scans row r from column cx for the first crossing
-// phi_i >= 0 > phi_{i+1}: row 0 is (cy, cz); rows 1..8 are y = cy +- 1..4 at z = cz;
-// rows 9..16 are z = cz +- 1..4 at y = cy.  Thread 0 then fits the parabola.
+// Tip tracking along +axis (0, 1, 2 = x, y, z of the kernel grid) from node c.  Warp r
+// scans line r from c[axis] for the first crossing phi_i >= 0 > phi_{i+1}: line 0 passes
+// through c; lines 1..8 are offset by j = +-1..+-4 along the first other axis b1, lines
+// 9..16 along the second other axis b2.  Thread 0 then fits the parabola
+// t(j) = t_tip - j^2/(2 rho) in each plane (axis, b) whose extent along b is more than one
+// node and averages the planes.
 template <typename T>
-__global__ void k_tip(const T* __restrict__ phi, int nx, int ny, int nz, int cx, int cy, int cz, int planes,
+__global__ void k_tip(const T* __restrict__ phi, int nx, int ny, int nz, int axis, int cx, int cy, int cz,
                       double* __restrict__ out) {
   __shared__ double cross[17];
   const int r = threadIdx.y, lane = threadIdx.x;
-  int yy = cy, zz = cz;
-  if (r >= 1 && r <= 8) {
-    const int j = (r <= 4) ? r : -(r - 4);
-    yy = cy + j;
-  } else if (r >= 9) {
-    const int j = (r <= 12) ? (r - 8) : -(r - 12);
-    zz = cz + j;
-  }
+  const int n[3] = {nx, ny, nz};
+  const int b1 = axis == 0 ? 1 : 0, b2 = axis == 2 ? 1 : 2;
+  int p[3] = {cx, cy, cz};
+  if (r >= 1 && r <= 8) p[b1] += (r <= 4) ? r : -(r - 4);
+  else if (r >= 9) p[b2] += (r <= 12) ? (r - 8) : -(r - 12);
   double res = -1.0;
-  if (yy >= 0 && yy < ny && zz >= 0 && zz < nz && cx >= 0) {
-    const long long row = ((long long)zz * ny + yy) * nx;
-    for (int base = cx; base + 1 < nx; base += 32) {
-      const int xi = base + lane;
+  if (p[0] >= 0 && p[0] < nx && p[1] >= 0 && p[1] < ny && p[2] >= 0 && p[2] < nz) {
+    const long long stride = axis == 0 ? 1 : (axis == 1 ? (long long)nx : (long long)nx * ny);
+    p[axis] = 0;
+    const long long line = ((long long)p[2] * ny + p[1]) * nx + p[0];
+    const int len = n[axis];
+    for (int base = axis == 0 ? cx : (axis == 1 ? cy : cz); base + 1 < len; base += 32) {
+      const int ti = base + lane;
       bool hit = false;
       T a = 0, b = 0;
-      if (xi + 1 < nx) {
-        a = phi[row + xi];
-        b = phi[row + xi + 1];
+      if (ti + 1 < len) {
+        a = phi[line + ti * stride];
+        b = phi[line + (ti + 1) * stride];
         hit = a >= T(0) && b < T(0);
       }
       const unsigned m = __ballot_sync(0xffffffffu, hit);
@@ -288,25 +291,27 @@ __global__ void k_tip(const T* __restrict__ phi, int nx, int ny, int nz, int cx,
   if (lane == 0) cross[r] = res;
   __syncthreads();
   if (r == 0 && lane == 0) {
-    const double xt = cross[0];
-    double rho[2] = {-1.0, -1.0};
+    const double tt = cross[0];
+    double sum = 0.0;
+    int planes = 0;
+    bool ok_all = true;
     for (int plane = 0; plane < 2; ++plane) {
+      if (n[plane == 0 ? b1 : b2] == 1) continue;  // no such plane on this grid
       double num = 0, den = 0;
-      bool ok = xt >= 0;
+      bool ok = tt >= 0;
       for (int q = 0; q < 8; ++q) {
         const int j = q < 4 ? q + 1 : -(q - 3);
-        const double xj = cross[1 + plane * 8 + q];
-        if (xj < 0) ok = false;
-        num += (double)(j * j) * (xt - xj);
+        const double tj = cross[1 + plane * 8 + q];
+        if (tj < 0) ok = false;
+        num += (double)(j * j) * (tt - tj);
         den += (double)(j * j) * (double)(j * j);
       }
-      if (ok && num > 0) rho[plane] = den / (2.0 * num);
+      if (ok && num > 0) sum += den / (2.0 * num);
+      else ok_all = false;
+      ++planes;
     }
-    out[0] = xt;
-    // planes: 0 both (averaged), 1 the xy plane alone, 2 the xz plane alone
-    if (planes == 1) out[1] = rho[0] > 0 ? rho[0] : -1.0;
-    else if (planes == 2) out[1] = rho[1] > 0 ? rho[1] : -1.0;
-    else out[1] = (rho[0] > 0 && rho[1] > 0) ? 0.5 * (rho[0] + rho[1]) : -1.0;
+    out[0] = tt;
+    out[1] = (planes > 0 && ok_all) ? sum / planes : -1.0;
   }
 }
 

@@ -2,14 +2,14 @@
 // allocate device memory.
 //
 // lbpf_sums reduces into a partials buffer that lbpf_create allocated.  Some
-// callers have device fields but may not allocate: code that runs while a
-// stream is being captured (cudaMalloc is not allowed there), latency-critical
-// loops that must avoid the implicit device synchronisation of cudaMalloc and
-// cudaFree, and hosts whose device memory is entirely reserved by another
-// allocator so that a fresh cudaMalloc would fail.  lbpf_field_sums_noalloc
-// serves them: its scratch is the file-scope array below, which exists once
-// per device for as long as the library is loaded.
+// callers have device fields but may not allocate: latency-critical loops that
+// must avoid the implicit device synchronisation of cudaMalloc and cudaFree, and
+// hosts whose device memory is entirely reserved by another allocator (a memory
+// pool sized to the whole device) so that a fresh cudaMalloc would fail.
+// lbpf_field_sums_noalloc serves them: its scratch is the file-scope array below,
+// which exists once per device for as long as the library is loaded.
 #include <math.h>
+#include <stdio.h>
 
 #include <mutex>
 
@@ -80,7 +80,10 @@ __global__ void k_sums_total(double* __restrict__ part, int nblk) {
   if (threadIdx.x < 4) part[4 * kMaxPartials + threadIdx.x] = acc[0][threadIdx.x];
 }
 
-// Device address of the scratch on the current device, looked up once per device.
+// Device address of the scratch on the current device, looked up once per device (the
+// first call on a device does this set-up).  The address belongs to that device's primary
+// context: after cudaDeviceReset the module is loaded again and the cached address is
+// stale, so a process that resets a device must not call this entry point on it again.
 int scratch_address(double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LBPF_ECUDA;
@@ -104,10 +107,18 @@ extern "C" int lbpf_field_sums_noalloc(const void* phi, const void* U, const voi
   if (!phi || !U || !out || n_sites < 1) return LBPF_EINVAL;
   if (storage < LBPF_F64 || storage > LBPF_BF16) return LBPF_EINVAL;
   if (n_sites > LBPF_NOALLOC_MAX_SITES) return LBPF_EINVAL;  // more partials than the scratch holds
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // the result is copied to host memory and the stream synchronised, which a stream under
+  // capture does not allow: refuse such a stream before enqueueing anything on it
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    fprintf(stderr, "lbpf_field_sums_noalloc: the stream is being captured; call it outside stream capture\n");
+    return LBPF_EINVAL;
+  }
   double* scratch = nullptr;
   int rc = scratch_address(&scratch);
   if (rc != LBPF_OK) return rc;
-  cudaStream_t st = (cudaStream_t)cuda_stream;
   const int nblk = (int)((n_sites + kSitesPerBlock - 1) / kSitesPerBlock);
   if (storage == LBPF_F64)
     k_sums_blocks<double><<<nblk, kThreads, 0, st>>>((const double*)phi, (const double*)U, (const double*)theta,

@@ -34,7 +34,7 @@ struct KernelTable {
   cudaError_t (*from_double)(cudaStream_t, void* out, const double* in, long long n);
   cudaError_t (*sums)(cudaStream_t, const void* phi, const void* U, const void* th, double theta0, double k,
                       long long n, double* part, int nblk);
-  cudaError_t (*tip)(cudaStream_t, const void* phi, int nx, int ny, int nz, int cx, int cy, int cz, int planes,
+  cudaError_t (*tip)(cudaStream_t, const void* phi, int nx, int ny, int nz, int axis, int cx, int cy, int cz,
                      double* out);
 };
 

@@ -70,9 +70,9 @@ struct AuxImpl {
     k_sums_final<<<1, 32, 0, st>>>(part, nblk, part + 4 * nblk, k, n, th == nullptr, theta0);
     return cudaGetLastError();
   }
-  static cudaError_t tip(cudaStream_t st, const void* phi, int nx, int ny, int nz, int cx, int cy, int cz,
-                         int planes, double* out) {
-    k_tip<T><<<1, dim3(32, 17), 0, st>>>((const T*)phi, nx, ny, nz, cx, cy, cz, planes, out);
+  static cudaError_t tip(cudaStream_t st, const void* phi, int nx, int ny, int nz, int axis, int cx, int cy, int cz,
+                         double* out) {
+    k_tip<T><<<1, dim3(32, 17), 0, st>>>((const T*)phi, nx, ny, nz, axis, cx, cy, cz, out);
     return cudaGetLastError();
   }
 };

@@ -18,7 +18,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "liblbpf.so")
 
-LBPF_OK, LBPF_EINVAL, LBPF_EUNSTABLE, LBPF_ENOMEM, LBPF_ENAN, LBPF_ETIMEOUT, LBPF_ECUDA = 0, -1, -2, -3, -4, -5, -6
+LBPF_OK, LBPF_EINVAL, LBPF_EUNSTABLE, LBPF_ENOMEM, LBPF_ENAN, LBPF_ECUDA = 0, -1, -2, -3, -4, -6
 STORAGE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 LBPF_PHI, LBPF_U, LBPF_THETA = 1, 2, 4
 
@@ -77,7 +77,7 @@ def load(path: str = LIB_PATH):
             "lbpf_read_fields": ([_VP, u32, _D, _D, _D], ctypes.c_int),
             "lbpf_step_timed": ([_VP, i64, _D], ctypes.c_int),
             "lbpf_sums": ([_VP, _D], ctypes.c_int),
-            "lbpf_tip": ([_VP, ctypes.POINTER(i32), _D, _D], ctypes.c_int),
+            "lbpf_tip": ([_VP, i32, _D, _D, _D], ctypes.c_int),
             "lbpf_steps_done": ([_VP], i64),
             "lbpf_save": ([_VP, ctypes.c_char_p], ctypes.c_int),
             "lbpf_load": ([_VP, ctypes.c_char_p], ctypes.c_int),
@@ -85,7 +85,10 @@ def load(path: str = LIB_PATH):
             "lbpf_get_tiling": ([_VP, ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
             "lbpf_autotune": ([_VP, i32, _D], ctypes.c_int),
             "lbpf_destroy": ([_VP], ctypes.c_int),
-            "lbpf_batch_create": ([i32, ctypes.POINTER(_VP), _VP, ctypes.POINTER(_VP)], ctypes.c_int),
+            "lbpf_batch_create": ([i32, ctypes.POINTER(Grid), ctypes.POINTER(Lattice), ctypes.POINTER(Params), _VP,
+                                   ctypes.POINTER(_VP)], ctypes.c_int),
+            "lbpf_batch_member": ([_VP, i32, ctypes.POINTER(_VP)], ctypes.c_int),
+            "lbpf_batch_from_sims": ([i32, ctypes.POINTER(_VP), _VP, ctypes.POINTER(_VP)], ctypes.c_int),
             "lbpf_batch_step": ([_VP, i64], ctypes.c_int),
             "lbpf_batch_set_tiling": ([_VP, i32, i32], ctypes.c_int),
             "lbpf_batch_destroy": ([_VP], ctypes.c_int),
@@ -122,11 +125,15 @@ def make_params(storage="f64", **kw) -> Params:
 class Sim:
     """One simulation on the current CUDA device (see ``lbpf_create``)."""
 
-    def __init__(self, shape, lattices=(19, 19, 0), storage="f64", stream=None, params=None, **kw):
+    def __init__(self, shape, lattices=(19, 19, 0), storage="f64", stream=None, params=None, _handle=None, **kw):
         self._L = load()
         self.nx, self.ny, self.nz = (int(v) for v in shape)
         self.q = tuple(int(v) for v in lattices)
         self.params = params if params is not None else make_params(storage, **kw)
+        self._owned = _handle is None
+        if _handle is not None:  # a batch member: the batch owns the handle
+            self._h = _handle
+            return
         h = _VP()
         rc = self._L.lbpf_create(ctypes.byref(Grid(self.nx, self.ny, self.nz)), ctypes.byref(Lattice(*self.q)),
                                  ctypes.byref(self.params), _VP(stream) if stream else None, ctypes.byref(h))
@@ -143,7 +150,8 @@ class Sim:
 
     def close(self):
         if getattr(self, "_h", None):
-            self._L.lbpf_destroy(self._h)
+            if self._owned:
+                self._L.lbpf_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -190,10 +198,11 @@ class Sim:
             _check(rc, "lbpf_sums")
         return out
 
-    def tip(self, centre):
-        c = (ctypes.c_int32 * 3)(*[int(v) for v in centre])
+    def tip(self, centre, axis=0):
+        """Tip coordinate along +axis from the node nearest `centre` and the tip radius."""
+        c = (ctypes.c_double * 3)(*[float(v) for v in centre])
         x, rho = ctypes.c_double(), ctypes.c_double()
-        _check(self._L.lbpf_tip(self._h, c, ctypes.byref(x), ctypes.byref(rho)), "lbpf_tip")
+        _check(self._L.lbpf_tip(self._h, int(axis), c, ctypes.byref(x), ctypes.byref(rho)), "lbpf_tip")
         return x.value, rho.value
 
     @property
@@ -221,16 +230,42 @@ class Sim:
 
 
 class Batch:
-    """Several simulations advanced together (see ``lbpf_batch_create``)."""
+    """Several simulations advanced together (see ``lbpf_batch_create``).
 
-    def __init__(self, sims, stream=None):
+    ``Batch(sims)`` batches existing :class:`Sim` handles (``lbpf_batch_from_sims``);
+    ``Batch.create(...)`` lets the library create and own the members."""
+
+    def __init__(self, sims, stream=None, _handle=None):
         self._L = load()
         self.sims = list(sims)
+        if _handle is not None:
+            self._h = _handle
+            return
         arr = (_VP * len(self.sims))(*[s.handle for s in self.sims])
         h = _VP()
-        _check(self._L.lbpf_batch_create(len(self.sims), arr, _VP(stream) if stream else None, ctypes.byref(h)),
-               "lbpf_batch_create")
+        _check(self._L.lbpf_batch_from_sims(len(self.sims), arr, _VP(stream) if stream else None, ctypes.byref(h)),
+               "lbpf_batch_from_sims")
         self._h = h
+
+    @classmethod
+    def create(cls, shapes, lattices, params, stream=None):
+        """n members from per-member shapes (nx, ny, nz), one lattice triple and per-member
+        :class:`Params` (``lbpf_batch_create``); members are :class:`Sim` views of handles
+        the batch owns."""
+        L = load()
+        n = len(shapes)
+        grids = (Grid * n)(*[Grid(*[int(v) for v in s]) for s in shapes])
+        lats = (Lattice * n)(*[Lattice(*[int(v) for v in lattices]) for _ in range(n)])
+        pars = (Params * n)(*params)
+        h = _VP()
+        _check(L.lbpf_batch_create(n, grids, lats, pars, _VP(stream) if stream else None, ctypes.byref(h)),
+               "lbpf_batch_create")
+        sims = []
+        for i in range(n):
+            m = _VP()
+            _check(L.lbpf_batch_member(h, i, ctypes.byref(m)), "lbpf_batch_member")
+            sims.append(Sim(shapes[i], lattices, params=params[i], _handle=m))
+        return cls(sims, _handle=h)
 
     def step(self, n=1):
         _check(self._L.lbpf_batch_step(self._h, int(n)), "lbpf_batch_step")
@@ -240,6 +275,9 @@ class Batch:
 
     def close(self):
         if getattr(self, "_h", None):
+            for s in self.sims:
+                if not s._owned:  # views of handles the batch destroys
+                    s._h = None
             self._L.lbpf_batch_destroy(self._h)
             self._h = None
 
@@ -248,6 +286,15 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def batch_from_workloads(ws, storage=None, stream=None):
+    """A library-owned batch (``lbpf_batch_create``) of the given workloads, each seeded."""
+    b = Batch.create([w.grid for w in ws], ws[0].lattices,
+                     [make_params(storage or w.storage, **w.params) for w in ws], stream=stream)
+    for w, s in zip(ws, b.sims):
+        s.init_seed(w.centres, w.radii, w.U0, w.theta0)
+    return b
 
 
 def sim_from_workload(w, storage=None, stream=None):

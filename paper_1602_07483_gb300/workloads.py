@@ -111,6 +111,20 @@ def large_kh(n: int = 512, storage: str = "f32") -> Workload:
                     U0=-0.5, theta0=-0.3, steps=4000, storage=storage)
 
 
+def dense_kh(n: int = 512, spacing: int = 64, R0: float = 20.0, storage: str = "f32") -> Workload:
+    """A stress case of the 512^3 two-harmonic workload with interface at most sites:
+    seeds of radius R0 on a cubic lattice of the given spacing (8^3 = 512 seeds at 512^3,
+    the first at spacing/2).  The seed profile's tails keep |grad phi|^2 above the
+    threshold of the undefined normal within about 12 cells of each surface, so the
+    anisotropy and anti-trapping arithmetic runs at over half of the sites, which a run
+    from four seeds reaches only after dendrite arms fill the box."""
+    g = np.arange(spacing // 2, n, spacing, dtype=np.float64)
+    c = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    p = base_params(aniso=1, eps1=-0.02, eps2=0.015, kappa=100.0, dt=0.01)
+    return Workload("dense%d_s%d_q19x3_%s" % (n, spacing, storage), (n, n, n), (19, 19, 19), p, c,
+                    np.full(len(c), R0), U0=-0.5, theta0=-0.3, steps=4000, storage=storage)
+
+
 def pure_substance_2d(n: int = 500, storage: str = "f64") -> Workload:
     """The 2D anisotropic benchmark of Sec. 4.1 (pure substance, Delta = 0.55):
     D2Q9 for phi, D2Q5 for theta, n^2 nodes (500^2 in the paper), dx = 0.4 W0,

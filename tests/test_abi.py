@@ -36,9 +36,41 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_strerror(lib):
-    for code in (0, -1, -2, -3, -4, -5, -6):
-        assert lib.lbpf_strerror(code)
+    for code in (0, -1, -2, -3, -4, -6):
+        assert lib.lbpf_strerror(code) != b"unknown error"
     assert b"unstable" in lib.lbpf_strerror(-2)
+    assert lib.lbpf_strerror(-5) == b"unknown error"  # no call has a bounded device wait
+
+
+def test_signatures_follow_the_boundary(lib):
+    """The declarations of the calls the method's boundary lists: the tip takes an axis and a
+    centre in lattice coordinates (doubles), and a batch is created from per-member grids,
+    lattices and parameters, with a second constructor over existing handles."""
+    src = open(os.path.join(ROOT, "include", "lbpf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    flat = " ".join(src.split())
+    assert "int lbpf_tip(lbpf_sim* sim, int32_t axis, const double centre_lu[3], double* x_tip_lu, double* rho_lu);" in flat
+    assert ("int lbpf_batch_create(int32_t n, const lbpf_grid* grids, const lbpf_lattice* lattices, "
+            "const lbpf_params* params, void* cuda_stream, lbpf_batch** out);") in flat
+    assert "int lbpf_batch_from_sims(int32_t n, lbpf_sim* const* sims, void* cuda_stream, lbpf_batch** out);" in flat
+    assert "int lbpf_batch_member(const lbpf_batch* batch, int32_t i, lbpf_sim** out);" in flat
+    assert "LBPF_ETIMEOUT" not in flat
+
+
+def test_batch_and_tip_reject_bad_arguments_without_gpu(lib):
+    """Argument checks that run before any device work."""
+    out = ctypes.c_void_p()
+    g = (lbpf.Grid * 2)(lbpf.Grid(8, 8, 8), lbpf.Grid(9, 8, 8))
+    la = (lbpf.Lattice * 2)(lbpf.Lattice(19, 19, 0), lbpf.Lattice(15, 19, 0))  # lattices differ
+    pa = (lbpf.Params * 2)(lbpf.make_params(storage="f32", dt=0.05), lbpf.make_params(storage="f32", dt=0.05))
+    assert lib.lbpf_batch_create(2, g, la, pa, None, ctypes.byref(out)) == lbpf.LBPF_EINVAL
+    assert lib.lbpf_batch_create(0, g, la, pa, None, ctypes.byref(out)) == lbpf.LBPF_EINVAL
+    assert lib.lbpf_batch_from_sims(1, None, None, ctypes.byref(out)) == lbpf.LBPF_EINVAL
+    c = (ctypes.c_double * 3)(1.0, 2.0, 3.0)
+    x = ctypes.c_double()
+    assert lib.lbpf_tip(None, 0, c, ctypes.byref(x), None) == lbpf.LBPF_EINVAL
+    m = ctypes.c_void_p()
+    assert lib.lbpf_batch_member(None, 0, ctypes.byref(m)) == lbpf.LBPF_EINVAL
 
 
 def _create(lattices=(19, 19, 0), grid=(8, 8, 8), **kw):

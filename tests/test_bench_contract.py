@@ -28,6 +28,9 @@ def test_reference_arm_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "GLUPS"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    # ms_per_step is the measured step of the sampled box; the 512^3 figure is labelled as implied
+    assert abs(d["ms_per_step"] - 64 ** 3 / (d["value"] * 1e9) * 1e3) < 1e-6 * d["ms_per_step"]
+    assert d["implied_ms_per_step_512"] > d["ms_per_step"]
 
 
 @pytest.mark.gpu
@@ -44,3 +47,5 @@ def test_own_arm_line_small():
     assert e["value"] > 0 and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
     assert d["gpu_launches"] == 2 * d["steps"]
     assert d["config"]["workload"].startswith("kh64")
+    dev = d["developed"]
+    assert dev["GLUPS"] > 0 and dev["after_steps"] >= 2000

@@ -94,6 +94,13 @@ def test_multistep_f64_2d_benchmark_setup():
     xo, ro = ora.tip((0, 0, 0))
     assert xg > 10 and abs(xg - xo) < 1e-9
     assert rg == ro == -1.0  # rows below the mirror corner do not exist
+    # along the paper's y axis (the kernel's z axis): the seed sits on the mirror corner, so
+    # the x <-> y symmetry of the set-up gives the same tip, and the oracle agrees
+    yg, _ = gpu.tip((0, 0, 0), axis=1)
+    yo, _ = ora.tip((0, 0, 0), axis=1)
+    assert abs(yg - yo) < 1e-9 and abs(yg - xg) < 1e-9
+    with pytest.raises(lbpf.LbpfError):
+        gpu.tip((0, 0, 0), axis=2)
 
 
 def test_f32_2d_phi_linf_after_200_steps():

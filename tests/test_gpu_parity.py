@@ -237,6 +237,101 @@ def test_batch_matches_single_bitwise(tiling):
             assert np.array_equal(x, y)
 
 
+BATCH_MEMBERS = [
+    # (shape, extra params, U0): uneven grids, anisotropy strengths, partition coefficients
+    ((33, 29, 23), dict(eps1=0.03, k=0.15), -0.55),
+    ((24, 31, 19), dict(eps1=0.05, k=0.1), -0.4),
+    ((40, 17, 21), dict(eps1=0.02, k=0.3), -0.3),
+    ((17, 22, 36), dict(eps1=0.04, k=0.15, antitrapping=0), -0.6),
+]
+
+
+def test_batch_members_match_oracle_f64():
+    """A library-owned batch (lbpf_batch_create) of four uneven FP64 simulations, each
+    started from its own noisy oracle state, tracks the oracle member by member: <= 1e-12
+    after one step, <= 1e-10 after 50 (one launch per kernel phase covers all members)."""
+    lat = (19, 19, 7)
+    states, oras, params = [], [], []
+    for m, (shape, extra, U0) in enumerate(BATCH_MEMBERS):
+        p = workloads.base_params(kappa=2.0, **extra)
+        g, h, f = noisy_state(shape, lat, p, seed=20 + m, U0=U0)
+        o = oracle.Sim(shape, lat, params=oracle_params(p))
+        o.set_state(g, h, f, theta0=-0.2)
+        states.append((g, h, f))
+        oras.append(o)
+        params.append(lbpf.make_params("f64", **p))
+    batch = lbpf.Batch.create([mb[0] for mb in BATCH_MEMBERS], lat, params)
+    for s, (g, h, f) in zip(batch.sims, states):
+        s.set_state(g, h, f, theta0=-0.2)
+    for steps, tol in ((1, REL_F64), (49, 1e-10)):
+        batch.step(steps)
+        for s, o in zip(batch.sims, oras):
+            o.step(steps)
+            for a, b in zip(s.read_fields(), o.fields()):
+                assert rel_err(a, b) <= tol, (s.nx, s.ny, s.nz, steps)
+    assert all(s.steps_done == 50 for s in batch.sims)
+    batch.close()
+
+
+def test_batch_f16_matches_single_bitwise():
+    """FP16 storage (the batched sweep's precision): a batch of uneven sweep members advances
+    each member bit for bit as the member would alone, through the library-owned form."""
+    ws = workloads.batch_sweep(count=3, storage="f16")
+    singles = [lbpf.sim_from_workload(w) for w in ws]
+    batch = lbpf.batch_from_workloads(ws)
+    batch.step(9)
+    for s in singles:
+        s.step(9)
+    for s, m in zip(singles, batch.sims):
+        assert m.steps_done == 9
+        for x, y in zip(s.read_fields(), m.read_fields()):
+            assert np.array_equal(x, y)
+    batch.close()
+
+
+def test_batch_orders_member_streams():
+    """Members on their own streams, the batch on another stream: a member read right after a
+    batch step (batch still open) sees the finished step, and a member seeded on its own
+    stream just before the step is seen by the batch."""
+    import torch
+    ws = workloads.batch_sweep(count=3, storage="f32")
+    singles = [lbpf.sim_from_workload(w) for w in ws]
+    members = [lbpf.Sim(w.grid, w.lattices, storage="f32", **w.params) for w in ws]
+    side = torch.cuda.Stream()
+    batch = lbpf.Batch(members, stream=side.cuda_stream)
+    for w, m in zip(ws, members):
+        m.init_seed(w.centres, w.radii, w.U0, w.theta0)   # enqueued on the member's stream
+    for k in range(3):
+        batch.step(5)
+        for s in singles:
+            s.step(5)
+        for s, m in zip(singles, members):
+            for x, y in zip(s.read_fields(), m.read_fields()):
+                assert np.array_equal(x, y), k
+    batch.close()
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_tip_along_each_axis_matches_oracle(axis):
+    """lbpf_tip along +x, +y, +z from a centre given in lattice coordinates (rounded to the
+    nearest node) agrees with the oracle's tip and radius on a grown 3D seed."""
+    w = workloads.coupled_dendrite(n=40)
+    ora = oracle.Sim(w.grid, w.lattices, params=oracle_params(w.params))
+    ora.init_seed(w.centres, w.radii, w.U0, w.theta0)
+    gpu = lbpf.sim_from_workload(w, storage="f64")
+    ora.step(60)
+    gpu.step(60)
+    c = [int(v) for v in w.centres[0]]
+    xg, rg = gpu.tip([v + 0.3 for v in c], axis=axis)
+    xo, ro = ora.tip(c, axis=axis)
+    assert xo > c[axis] and ro > 0
+    assert abs(xg - xo) < 1e-9 and abs(rg - ro) < 1e-7
+    with pytest.raises(lbpf.LbpfError):
+        gpu.tip([-3, 0, 0], axis=axis)
+    with pytest.raises(lbpf.LbpfError):
+        gpu.tip(c, axis=3)
+
+
 def test_batch_set_tiling_rejects_bad_values():
     members = [lbpf.sim_from_workload(w) for w in workloads.batch_sweep(count=2, storage="f32")]
     batch = lbpf.Batch(members)

@@ -62,6 +62,25 @@ def test_tip_radius_of_exact_parabola():
     assert abs(rho - 0.5 * (ra + rb)) < 1e-10 * ra
 
 
+@pytest.mark.parametrize("axis", [1, 2])
+def test_tip_along_other_axes_of_exact_parabola(axis):
+    """The same exact-parabola pin for a scan along +y or +z: the crossings lie on
+    t = t_tip - j^2/(2 rho_b) in the plane of the scan axis and each other axis b."""
+    n, c = (13, 13, 13), [6, 6, 6]
+    shape = list(n)
+    shape[axis] = 40
+    others = [b for b in range(3) if b != axis]
+    rb = {others[0]: 6.5, others[1]: 11.0}
+    tt = 29.3
+    Z, Y, X = np.meshgrid(np.arange(shape[2]), np.arange(shape[1]), np.arange(shape[0]), indexing="ij")
+    P = (X, Y, Z)
+    T = tt - sum((P[b] - c[b]) ** 2 / (2 * rb[b]) for b in others)
+    s = _sim_with_phi(0.37 * (T - P[axis]))
+    t_tip, rho = s.tip(c, axis=axis)
+    assert abs(t_tip - tt) < 1e-12
+    assert abs(rho - 0.5 * (rb[others[0]] + rb[others[1]])) < 1e-10 * 6.5
+
+
 def test_tip_radius_of_exact_parabola_2d():
     """On an nz = 1 grid only the xy plane exists: the radius is that plane's fit alone."""
     shape, c = (36, 11, 1), (5, 5, 0)
@@ -71,6 +90,13 @@ def test_tip_radius_of_exact_parabola_2d():
     x_tip, rho = s.tip(c)
     assert abs(x_tip - xt) < 1e-12
     assert abs(rho - ra) < 1e-10 * ra
+    # along the grid's y axis: the plane is the same, the roles of the axes swap
+    yt, ry = 7.5, 3.0
+    Y, X = np.meshgrid(np.arange(24), np.arange(17), indexing="ij")
+    s2 = _sim_with_phi((0.37 * (yt - (X - 8) ** 2 / (2 * ry) - Y))[None], lattices=(9, 5, 0))
+    y_tip, rho2 = s2.tip((8, 0, 0), axis=1)
+    assert abs(y_tip - yt) < 1e-12
+    assert abs(rho2 - ry) < 1e-10 * ry
 
 
 @pytest.mark.parametrize("R", [20.0, 40.0])
