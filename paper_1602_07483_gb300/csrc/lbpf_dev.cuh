@@ -233,12 +233,16 @@ struct NYOf<0> {
 // FP32; `shift` removes the bulk value so the stored number is the small part.
 template <typename S>
 struct Codec;
+// raw(s) / pack(v): the stored number itself as T and back (round to nearest), for
+// arithmetic done directly in the scaled units (f - shift) * scale.
 template <>
 struct Codec<double> {
   using T = double;
   static constexpr bool shifted = false;
   __device__ static __forceinline__ T dec(double s, T, T) { return s; }
   __device__ static __forceinline__ double enc(T v, T, T) { return v; }
+  __device__ static __forceinline__ T raw(double s) { return s; }
+  __device__ static __forceinline__ double pack(T v) { return v; }
 };
 template <>
 struct Codec<float> {
@@ -246,6 +250,8 @@ struct Codec<float> {
   static constexpr bool shifted = false;
   __device__ static __forceinline__ T dec(float s, T, T) { return s; }
   __device__ static __forceinline__ float enc(T v, T, T) { return v; }
+  __device__ static __forceinline__ T raw(float s) { return s; }
+  __device__ static __forceinline__ float pack(T v) { return v; }
 };
 template <>
 struct Codec<__half> {
@@ -255,6 +261,8 @@ struct Codec<__half> {
     return fmaf(__half2float(s), inv_scale, shift);
   }
   __device__ static __forceinline__ __half enc(T v, T shift, T scale) { return __float2half_rn((v - shift) * scale); }
+  __device__ static __forceinline__ T raw(__half s) { return __half2float(s); }
+  __device__ static __forceinline__ __half pack(T v) { return __float2half_rn(v); }
 };
 template <>
 struct Codec<__nv_bfloat16> {
@@ -266,6 +274,8 @@ struct Codec<__nv_bfloat16> {
   __device__ static __forceinline__ __nv_bfloat16 enc(T v, T shift, T scale) {
     return __float2bfloat16_rn((v - shift) * scale);
   }
+  __device__ static __forceinline__ T raw(__nv_bfloat16 s) { return __bfloat162float(s); }
+  __device__ static __forceinline__ __nv_bfloat16 pack(T v) { return __float2bfloat16_rn(v); }
 };
 
 // ---------------------------------------------------------------- descriptors
@@ -528,16 +538,12 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_PHI
           for (int i = 0; i < QP; ++i) {
             const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
             if (!row_needs(ey)) continue;
-            const T wi = (T)L::w(i);
             const unsigned own = (unsigned)i * NS + site;
             const unsigned off = (unsigned)(ez * (int)plane + ey * nx + ex);
-            T shift_in = 0, shift_nl = 0;
-            if (C::shifted) {
-              shift_in = wi * (ringm + slot4(zc - ez) * RS)[rc - ey * RW - ex];
-              shift_nl = wi * (ringm + slot4(zc) * RS)[rc];
-            }
-            gpull[i] = C::dec(ldro(gin + (own - off)), shift_in, iscale);
-            gnl[i] = C::dec(ldro(gin + own), shift_nl, iscale);
+            gpull[i] = C::raw(ldro(gin + (own - off)));
+            if (C::shifted)  // stored units with the source's shift: Gp + S w phi_ref(src)
+              gpull[i] = fma(rmul(scale, (T)L::w(i)), (ringm + slot4(zc - ez) * RS)[rc - ey * RW - ex], gpull[i]);
+            gnl[i] = C::raw(ldro(gin + own));
           }
         } else {
           // wall node: bounce-back for links from outside, standard collision (no non-local term)
@@ -545,17 +551,14 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_PHI
           for (int i = 0; i < QP; ++i) {
             const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
             if (!row_needs(ey)) continue;
-            const T wi = (T)L::w(i);
             const int sx = x - ex, sy = y - ey, sz = zc - ez;
             const bool inside = sx >= 0 && sx < nx && sy >= 0 && sy < ny && sz >= 0 && sz < nz;
             const unsigned src = inside ? site - (unsigned)(ez * (int)plane + ey * nx + ex) : site;
             const int ii = inside ? i : L::opp(i);
-            T shift_in = 0;
-            if (C::shifted) {
-              const T* Rs = ringm + slot4(inside ? sz : zc) * RS;
-              shift_in = wi * Rs[inside ? rc - ey * RW - ex : rc];
-            }
-            gpull[i] = C::dec(ldro(gin + ((unsigned)ii * NS + src)), shift_in, iscale);
+            gpull[i] = C::raw(ldro(gin + ((unsigned)ii * NS + src)));
+            if (C::shifted)
+              gpull[i] = fma(rmul(scale, (T)L::w(i)), (ringm + slot4(inside ? sz : zc) * RS)[inside ? rc - ey * RW - ex : rc],
+                             gpull[i]);
             gnl[i] = T(0);
           }
         }
@@ -581,7 +584,13 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_PHI
         const T omw = T(1) - inv_eta;
         const T kph = radd(rmul(inv_eta, ph), Qdt);
         const T ncN = rmul(inv_eta, c_N);
-        T Kc[3], nxc[3], nyc[3], nzc[3];
+        T Kc[3], nxc[3], nyc[3], nzc[3], Sc[3];
+        // FP16/BF16: the populations stay in the stored units G = (g - w phi_ref) S, phi_ref
+        // the phi of the step before at the node that stored them (phi^{n-1}); with
+        // Gp' = Gp + S w phi_ref(src) (pulled) and G* = (g* - w phi^n) S the collision becomes
+        //   G* = [omw Gp' - oma2 Gn + S (eq - w (oma2 phi_ref(x) + a^2 phi^n))] / a^2
+        // and the value gathered for phi^{n+1} is G* + S w phi^n
+        const T phr_x = C::shifted ? (ringm + slot4(zc) * RS)[rc] : T(0);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const T wc = (T)L::w(c == 0 ? 0 : (c == 1 ? 1 : L::diag0));
@@ -590,22 +599,27 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_PHI
           nxc[c] = rmul(nc, Nx);
           nyc[c] = rmul(nc, Ny);
           nzc[c] = rmul(nc, Nz);
+          if (C::shifted) {
+            Kc[c] = rmul(scale, radd(Kc[c], -rmul(wc, radd(rmul(oma2, phr_x), rmul(a2, ph)))));
+            nxc[c] = rmul(scale, nxc[c]);
+            nyc[c] = rmul(scale, nyc[c]);
+            nzc[c] = rmul(scale, nzc[c]);
+            Sc[c] = rmul(scale, rmul(wc, ph));
+          }
         }
 #pragma unroll
         for (int i = 0; i < QP; ++i) {
           const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
           if (!row_needs(ey)) continue;
           const int c = L::cls(i);
-          const T wi = (T)L::w(i);
           T eq = Kc[c];
           if (ex) eq = radd(eq, ex > 0 ? nxc[c] : -nxc[c]);
           if (ey) eq = radd(eq, ey > 0 ? nyc[c] : -nyc[c]);
           if (ez) eq = radd(eq, ez > 0 ? nzc[c] : -nzc[c]);
           const T g = rmul(fma(-oma2, gnl[i], fma(gpull[i], omw, eq)), inv_a2);
-          const T shift_out = C::shifted ? wi * ph : T(0);
-          const auto enc = C::enc(g, shift_out, scale);
+          const auto enc = C::pack(g);
           if (store) gout[(unsigned)i * NS + site] = enc;
-          gs[i] = C::shifted ? C::dec(enc, shift_out, iscale) : g;
+          gs[i] = C::shifted ? radd(C::raw(enc), Sc[c]) : g;
           if (ey != 0) sGb[YS::slot(i) * PS + ly * 32 + tx] = gs[i];
         }
       }
@@ -698,8 +712,10 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_PHI
           }
         }
         const int zw = zc - 1;
-        if (zw >= it.z0 && zw < it.z1 && zw >= 0) phinew[((unsigned)zw * ny + y) * (unsigned)nx + x] = acc0;
-        if (zc == nz - 1 && zc >= it.z0 && zc < it.z1) phinew[((unsigned)zc * ny + y) * (unsigned)nx + x] = acc1;
+        // FP16/BF16: the gathered values are in stored units (scale is a power of two)
+        auto mP = [&](T a) { return C::shifted ? rmul(a, iscale) : a; };
+        if (zw >= it.z0 && zw < it.z1 && zw >= 0) phinew[((unsigned)zw * ny + y) * (unsigned)nx + x] = mP(acc0);
+        if (zc == nz - 1 && zc >= it.z0 && zc < it.z1) phinew[((unsigned)zc * ny + y) * (unsigned)nx + x] = mP(acc1);
       }
       acc0 = acc1;
       acc1 = acc2;
@@ -808,15 +824,13 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_UTH
           for (int i = 0; i < QU; ++i) {
             const int ex = LU::ex(i), ey = LU::ey(i), ez = LU::ez(i);
             if (!row_needs(ey)) continue;
-            const T sh = C::shifted ? (T)LU::w(i) * sh_h : T(0);
-            hs[i] = C::dec(ldro(hin + ((unsigned)i * NS + site - (unsigned)(ez * (int)plane + ey * nx + ex))), sh, isc_h);
+            hs[i] = C::raw(ldro(hin + ((unsigned)i * NS + site - (unsigned)(ez * (int)plane + ey * nx + ex))));
           }
 #pragma unroll
           for (int i = 0; i < QT; ++i) {
             const int ex = LT::ex(i), ey = LT::ey(i), ez = LT::ez(i);
             if (!row_needs(ey)) continue;
-            const T sh = C::shifted ? (T)LT::w(i) * sh_f : T(0);
-            fs[i] = C::dec(ldro(fin + ((unsigned)i * NS + site - (unsigned)(ez * (int)plane + ey * nx + ex))), sh, isc_f);
+            fs[i] = C::raw(ldro(fin + ((unsigned)i * NS + site - (unsigned)(ez * (int)plane + ey * nx + ex))));
           }
         } else {
 #pragma unroll
@@ -827,8 +841,7 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_UTH
             const bool inside = sx >= 0 && sx < nx && sy >= 0 && sy < ny && sz >= 0 && sz < nz;
             const unsigned src = inside ? site - (unsigned)(ez * (int)plane + ey * nx + ex) : site;
             const int ii = inside ? i : LU::opp(i);
-            const T sh = C::shifted ? (T)LU::w(i) * sh_h : T(0);
-            hs[i] = C::dec(ldro(hin + ((unsigned)ii * NS + src)), sh, isc_h);
+            hs[i] = C::raw(ldro(hin + ((unsigned)ii * NS + src)));
           }
 #pragma unroll
           for (int i = 0; i < QT; ++i) {
@@ -838,8 +851,7 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_UTH
             const bool inside = sx >= 0 && sx < nx && sy >= 0 && sy < ny && sz >= 0 && sz < nz;
             const unsigned src = inside ? site - (unsigned)(ez * (int)plane + ey * nx + ex) : site;
             const int ii = inside ? i : LT::opp(i);
-            const T sh = C::shifted ? (T)LT::w(i) * sh_f : T(0);
-            fs[i] = C::dec(ldro(fin + ((unsigned)ii * NS + src)), sh, isc_f);
+            fs[i] = C::raw(ldro(fin + ((unsigned)ii * NS + src)));
           }
         }
         // phi^{n+1} at the node and its six neighbours (mirror ghosts)
@@ -909,38 +921,45 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_UTH
           jxc[c] = rmul(jc, Jx);
           jyc[c] = rmul(jc, Jy);
           jzc[c] = rmul(jc, Jz);
+          if (C::shifted) {
+            // FP16/BF16: the populations stay in the stored units H = (h - w U0) S, so
+            // H* = H (1 - 1/eta_U) + S (h0/eta_U + w src dt - w U0 / eta_U)
+            KU[c] = rmul(sc_h, radd(KU[c], -rmul(rmul(wc, sh_h), inv_etaU)));
+            jxc[c] = rmul(sc_h, jxc[c]);
+            jyc[c] = rmul(sc_h, jyc[c]);
+            jzc[c] = rmul(sc_h, jzc[c]);
+          }
         }
 #pragma unroll
         for (int i = 0; i < QU; ++i) {
           const int ex = LU::ex(i), ey = LU::ey(i), ez = LU::ez(i);
           if (!row_needs(ey)) continue;
           const int c = LU::cls(i);
-          const T wi = (T)LU::w(i);
-          const T sh = C::shifted ? wi * sh_h : T(0);
           T eq = KU[c];
           if (ex) eq = radd(eq, ex > 0 ? jxc[c] : -jxc[c]);
           if (ey) eq = radd(eq, ey > 0 ? jyc[c] : -jyc[c]);
           if (ez) eq = radd(eq, ez > 0 ? jzc[c] : -jzc[c]);
           const T h = fma(hs[i], omU, eq);
-          const auto enc = C::enc(h, sh, sc_h);
+          const auto enc = C::pack(h);
           if (store) hout[(unsigned)i * NS + site] = enc;
-          hs[i] = C::shifted ? C::dec(enc, sh, isc_h) : h;
+          hs[i] = C::raw(enc);
           if (ey != 0) sHb[YU::slot(i) * PS + ly * 32 + tx] = hs[i];
         }
         if (QT > 0) {
           // f* = f (1 - 1/eta_T) + w (theta/eta_T + Q_theta dt) with Q_theta dt = dphi / 2
           const T omT = T(1) - inv_etaT;
-          const T kT = radd(rmul(inv_etaT, th), rmul(T(0.5), dphi));
+          T kT = radd(rmul(inv_etaT, th), rmul(T(0.5), dphi));
+          // FP16/BF16: F* = F (1 - 1/eta_T) + w S (theta/eta_T + dphi/2 - theta0/eta_T) in stored units
+          if (C::shifted) kT = rmul(sc_f, radd(kT, -rmul(sh_f, inv_etaT)));
 #pragma unroll
           for (int i = 0; i < QT; ++i) {
             const int ey = LT::ey(i);
             if (!row_needs(ey)) continue;
             const T wi = (T)LT::w(i);
-            const T sh = C::shifted ? wi * sh_f : T(0);
             const T f = fma(fs[i], omT, rmul(wi, kT));
-            const auto enc = C::enc(f, sh, sc_f);
+            const auto enc = C::pack(f);
             if (store) fout[(unsigned)i * NS + site] = enc;
-            fs[i] = C::shifted ? C::dec(enc, sh, isc_f) : f;
+            fs[i] = C::raw(enc);
             if (ey != 0) sFb[YT::slot(i) * PS + ly * 32 + tx] = fs[i];
           }
         }
@@ -1078,15 +1097,19 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_UTH
           }
         }
         const int zw = zc - 1;
+        // FP16/BF16: the gathered sums are in stored units; the shifts w_i U0 (w_i theta0)
+        // of the populations arriving at a node add up to U0 (theta0)
+        auto mU = [&](T a) { return C::shifted ? fma(a, isc_h, sh_h) : a; };
+        auto mT = [&](T a) { return C::shifted ? fma(a, isc_f, sh_f) : a; };
         if (zw >= it.z0 && zw < it.z1 && zw >= 0) {
           const unsigned sw = ((unsigned)zw * ny + y) * (unsigned)nx + x;
-          Unew[sw] = u0;
-          if (QT > 0) thnew[sw] = t0;
+          Unew[sw] = mU(u0);
+          if (QT > 0) thnew[sw] = mT(t0);
         }
         if (zc == nz - 1 && zc >= it.z0 && zc < it.z1) {
           const unsigned sw = ((unsigned)zc * ny + y) * (unsigned)nx + x;
-          Unew[sw] = u1;
-          if (QT > 0) thnew[sw] = t1;
+          Unew[sw] = mU(u1);
+          if (QT > 0) thnew[sw] = mT(t1);
         }
       }
       u0 = u1;
