@@ -244,6 +244,12 @@ def run_own(args):
     ms_phi, ms_uth, ms_span = sim.step_timed(args.steps)
     barrier_sync()
     clk = clocks.stop()
+    # the FP64 diagnostics reduction (lbpf_sums: four sums over all sites, read back to the host)
+    sim.sums(check=False)
+    t0 = time.perf_counter()
+    for _ in range(10):
+        sim.sums(check=False)
+    sums_ms = (time.perf_counter() - t0) / 10 * 1e3
     developed = None
     if args.developed and rank == 0 and world == 1 and args.workload == "kh":
         # the same simulation after it has grown for `developed` steps from the seeds
@@ -341,6 +347,7 @@ def run_own(args):
             "gpu_launches": 2 * args.steps,
             "clocks": clk,
             "developed": developed,
+            "sums_ms": sums_ms,
             "variants": variants,
         }
         print(json.dumps(line), flush=True)

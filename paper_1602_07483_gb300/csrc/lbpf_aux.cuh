@@ -193,18 +193,49 @@ __global__ void k_unpack(SimDev sd, int field, int par, LatRT L, int i, double* 
   }
 }
 
+// h + l += x for a float-float accumulator (h, l): an error-free sum of h and x (TwoSum,
+// Knuth) whose rounding error goes into l.  The explicit _rn operations keep the compiler
+// from contracting or reordering them.
+__device__ __forceinline__ void ff_acc(float& h, float& l, float x) {
+  const float s = __fadd_rn(h, x);
+  const float bp = __fsub_rn(s, h);
+  const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+  h = s;
+  l = __fadd_rn(l, err);
+}
+
 // FP64 partial sums per block: [sum phi, sum U, sum theta, sum phi U].
 template <typename T>
 __global__ void k_sums(const T* __restrict__ phi, const T* __restrict__ U, const T* __restrict__ th, double theta0,
                        double k, long long n, double* __restrict__ part) {
   // sum phi, sum U, sum theta and sum phi U; the total solute follows from them (k_sums_final)
   double a = 0, b = 0, c = 0, e = 0;
-  for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
-    const double p = (double)phi[s], u = (double)U[s];
-    a += p;
-    b += u;
-    if (th) c += (double)th[s];
-    e = fma(p, u, e);
+  if constexpr (sizeof(T) == 8) {
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+      const double p = (double)phi[s], u = (double)U[s];
+      a += p;
+      b += u;
+      if (th) c += (double)th[s];
+      e = fma(p, u, e);
+    }
+  } else {
+    // FP32 fields: each thread accumulates in float-float (about 48 significant bits; the
+    // product phi U is split exactly into p u + fma(p, u, -p u)), which uses the FP32 pipes
+    // instead of GB300's narrow FP64 pipe; the partials are then reduced in FP64
+    float ah = 0, al = 0, bh = 0, bl = 0, ch = 0, cl = 0, eh = 0, el = 0;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n; s += (long long)gridDim.x * blockDim.x) {
+      const float p = (float)phi[s], u = (float)U[s];
+      ff_acc(ah, al, p);
+      ff_acc(bh, bl, u);
+      if (th) ff_acc(ch, cl, (float)th[s]);
+      const float pr = __fmul_rn(p, u);
+      ff_acc(eh, el, pr);
+      el = __fadd_rn(el, fmaf(p, u, -pr));
+    }
+    a = (double)ah + (double)al;
+    b = (double)bh + (double)bl;
+    c = (double)ch + (double)cl;
+    e = (double)eh + (double)el;
   }
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_down_sync(0xffffffffu, a, o);
