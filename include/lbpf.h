@@ -156,8 +156,11 @@ int lbpf_tip(lbpf_sim* sim, int32_t axis, const double centre_lu[3], double* x_t
 int64_t lbpf_steps_done(const lbpf_sim* sim);
 
 /* Checkpoint: write / read a self-describing binary file (header with grid,
- * lattices, parameters, step count, then the post-streaming populations in
- * FP64).  lbpf_load requires a handle created with the same grid and lattices. */
+ * lattices, parameters, step count; then the post-streaming populations and the
+ * moment fields phi^n, phi^{n-1}, U^n, theta^n, theta^{n-1}, all in FP64), so that a
+ * run restarts bit for bit in every storage type (the FP16/BF16 codec is shifted by
+ * phi^{n-1} and theta^{n-1}, and decodes to FP64 exactly).  lbpf_load requires a handle
+ * created with the same grid and lattices, and a file of this format (version 3). */
 int lbpf_save(lbpf_sim* sim, const char* path);
 int lbpf_load(lbpf_sim* sim, const char* path);
 

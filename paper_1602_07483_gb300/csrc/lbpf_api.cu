@@ -90,7 +90,7 @@ struct lbpf_sim {
   void* pop[2][3] = {};
   void* phi[3] = {};
   void* U[2] = {};
-  void* th[2] = {};
+  void* th[3] = {};  // theta levels like phi (theta^{n-1} is the FP16/BF16 shift of f)
   SimDev hd{};
   SimDev* dd = nullptr;
   WorkItem* d_items = nullptr;
@@ -281,7 +281,8 @@ void fill_dev(lbpf_sim* s) {
   for (int b = 0; b < 2; ++b)
     for (int f = 0; f < 3; ++f) d.pop[b][f] = s->pop[b][f];
   for (int l = 0; l < 3; ++l) d.phi[l] = s->phi[l];
-  for (int b = 0; b < 2; ++b) { d.U[b] = s->U[b]; d.th[b] = s->th[b]; }
+  for (int b = 0; b < 2; ++b) d.U[b] = s->U[b];
+  for (int l = 0; l < 3; ++l) d.th[l] = s->th[l];
   const double e2p = lattice_e2(s->lat.q_phi), e2u = lattice_e2(s->lat.q_u);
   const double W2t = p.W0 * p.W0 / p.tau0;
   d.inv2dx = 1.0 / (2.0 * p.dx);
@@ -324,10 +325,10 @@ void free_sim(lbpf_sim* s) {
   for (int b = 0; b < 2; ++b)
     for (int f = 0; f < 3; ++f) if (s->pop[b][f]) cudaFree(s->pop[b][f]);
   for (int l = 0; l < 3; ++l) if (s->phi[l]) cudaFree(s->phi[l]);
-  for (int b = 0; b < 2; ++b) {
+  for (int b = 0; b < 2; ++b)
     if (s->U[b]) cudaFree(s->U[b]);
-    if (s->th[b]) cudaFree(s->th[b]);
-  }
+  for (int l = 0; l < 3; ++l)
+    if (s->th[l]) cudaFree(s->th[l]);
   if (s->dd) cudaFree(s->dd);
   if (s->d_items) cudaFree(s->d_items);
   if (s->d_part) cudaFree(s->d_part);
@@ -395,10 +396,8 @@ int lbpf_create(const lbpf_grid* grid, const lbpf_lattice* lattice, const lbpf_p
     for (int f = 0; f < 3 && ok; ++f)
       if (qs[f]) ok = cudaMalloc(&s->pop[b][f], (size_t)qs[f] * N * s->kt->sbytes) == cudaSuccess;
   for (int l = 0; l < 3 && ok; ++l) ok = cudaMalloc(&s->phi[l], N * s->kt->tbytes) == cudaSuccess;
-  for (int b = 0; b < 2 && ok; ++b) {
-    ok = cudaMalloc(&s->U[b], N * s->kt->tbytes) == cudaSuccess;
-    if (ok && lattice->q_theta) ok = cudaMalloc(&s->th[b], N * s->kt->tbytes) == cudaSuccess;
-  }
+  for (int b = 0; b < 2 && ok; ++b) ok = cudaMalloc(&s->U[b], N * s->kt->tbytes) == cudaSuccess;
+  for (int l = 0; l < 3 && ok && lattice->q_theta; ++l) ok = cudaMalloc(&s->th[l], N * s->kt->tbytes) == cudaSuccess;
   s->npart = 1024;
   if (ok) ok = cudaMalloc(&s->d_part, sizeof(double) * (4 * s->npart + 8)) == cudaSuccess;
   if (ok) ok = cudaMalloc(&s->d_small, sizeof(double) * 8) == cudaSuccess;
@@ -414,10 +413,9 @@ int lbpf_create(const lbpf_grid* grid, const lbpf_lattice* lattice, const lbpf_p
     for (int f = 0; f < 3; ++f)
       if (s->pop[b][f]) cudaMemsetAsync(s->pop[b][f], 0, (size_t)qs[f] * N * s->kt->sbytes, s->stream);
   for (int l = 0; l < 3; ++l) cudaMemsetAsync(s->phi[l], 0, N * s->kt->tbytes, s->stream);
-  for (int b = 0; b < 2; ++b) {
-    cudaMemsetAsync(s->U[b], 0, N * s->kt->tbytes, s->stream);
-    if (s->th[b]) cudaMemsetAsync(s->th[b], 0, N * s->kt->tbytes, s->stream);
-  }
+  for (int b = 0; b < 2; ++b) cudaMemsetAsync(s->U[b], 0, N * s->kt->tbytes, s->stream);
+  for (int l = 0; l < 3; ++l)
+    if (s->th[l]) cudaMemsetAsync(s->th[l], 0, N * s->kt->tbytes, s->stream);
   s->fphi = s->kt->phi[q_index(lattice->q_phi)];
   s->futh = s->kt->uth[q_index(lattice->q_u)][qt_index(lattice->q_theta)];
   // 32 x 8 blocks: two resident blocks per SM at 128 registers per thread
@@ -468,6 +466,9 @@ int lbpf_init_seed(lbpf_sim* s, int32_t n, const double* centres, const double* 
   if (s->lat.q_theta) Lt = make_lat_rt(s->lat.q_theta);
   CK(s, s->kt->init_pop(s->stream, s->hd, Lp, Lu, Lt, s->phi[1], U0, theta0));
   CK(s, cudaMemcpyAsync(s->phi[2], s->phi[1], (size_t)s->nsite * s->kt->tbytes, cudaMemcpyDeviceToDevice, s->stream));
+  // theta^{n-1} (the codec reference of f) = the initial theta
+  if (s->th[0])
+    CK(s, cudaMemcpyAsync(s->th[2], s->th[0], (size_t)s->nsite * s->kt->tbytes, cudaMemcpyDeviceToDevice, s->stream));
   CK(s, cudaStreamSynchronize(s->stream));
   cudaFree(d_seed);
   s->steps = 0;
@@ -543,7 +544,7 @@ int lbpf_read_fields(lbpf_sim* s, uint32_t mask, double* phi, double* U, double*
   if (s->sticky) return s->sticky;
   if (((mask & LBPF_PHI) && !phi) || ((mask & LBPF_U) && !U) || ((mask & LBPF_THETA) && !theta)) return LBPF_EINVAL;
   const size_t N = (size_t)s->nsite;
-  const void* src[3] = {s->phi[s6_of(s) % 3], s->U[par_of(s)], s->lat.q_theta ? s->th[par_of(s)] : nullptr};
+  const void* src[3] = {s->phi[s6_of(s) % 3], s->U[par_of(s)], s->lat.q_theta ? s->th[s6_of(s) % 3] : nullptr};
   double* dst[3] = {(mask & LBPF_PHI) ? phi : nullptr, (mask & LBPF_U) ? U : nullptr,
                     (mask & LBPF_THETA) ? theta : nullptr};
   const bool need_tmp = s->kt->tbytes != 8;
@@ -572,7 +573,7 @@ int lbpf_read_fields(lbpf_sim* s, uint32_t mask, double* phi, double* U, double*
 int lbpf_sums(lbpf_sim* s, double out[4]) {
   if (!s || !out) return LBPF_EINVAL;
   if (s->sticky) return s->sticky;
-  const void* th = s->lat.q_theta ? s->th[par_of(s)] : nullptr;
+  const void* th = s->lat.q_theta ? s->th[s6_of(s) % 3] : nullptr;
   const int nblk = (int)std::min<long long>(s->npart, std::max<long long>(1, (s->nsite + 255) / 256));
   CK(s, s->kt->sums(s->stream, s->phi[s6_of(s) % 3], s->U[par_of(s)], th, s->theta0, s->p.k, s->nsite, s->d_part,
                     nblk));
@@ -612,9 +613,9 @@ int lbpf_tip(lbpf_sim* s, int32_t axis, const double centre_lu[3], double* x_tip
 }
 
 namespace {
-// Import post-streaming populations.  `moments` (optional, FP64, 4 x nsite):
-// phi^n, phi^{n-1}, U^n, theta^n to install instead of recomputing the moments
-// from the populations, so that a checkpoint restarts bit for bit.
+// Import post-streaming populations.  `moments` (optional, FP64, 5 x nsite):
+// phi^n, phi^{n-1}, U^n, theta^n, theta^{n-1} to install instead of recomputing the
+// moments from the populations, so that a checkpoint restarts bit for bit.
 int import_state(lbpf_sim* s, const double* g, const double* h, const double* f, double theta0,
                  const double* moments) {
   int rc = ensure_tmp(s);
@@ -634,7 +635,7 @@ int import_state(lbpf_sim* s, const double* g, const double* h, const double* f,
     if (!qs[fld]) continue;
     const LatRT L = make_lat_rt(qs[fld]);
     if (moments) {
-      const double* m = moments + (size_t)(fld == 0 ? 0 : fld + 1) * N;
+      const double* m = moments + (size_t)(fld == 0 ? 0 : (fld == 1 ? 2 : 3)) * N;
       CK(s, cudaMemcpyAsync(acc, m, N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     } else {
       // moments: sum over i in index order, in FP64
@@ -646,13 +647,16 @@ int import_state(lbpf_sim* s, const double* g, const double* h, const double* f,
       }
     }
     CK(s, s->kt->from_double(s->stream, mom[fld], acc, (long long)N));
-    if (fld == 0) {
-      // codec reference phi^{n-1}: the saved level, or phi^n for an imported state
+    void* prev = fld == 0 ? s->phi[2] : (fld == 2 ? s->th[2] : nullptr);
+    if (prev) {
+      // codec reference of g and f, phi^{n-1} and theta^{n-1}: the saved level, or the
+      // current one for an imported state
       if (moments) {
-        CK(s, cudaMemcpyAsync(acc, moments + N, N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-        CK(s, s->kt->from_double(s->stream, s->phi[2], acc, (long long)N));
+        CK(s, cudaMemcpyAsync(acc, moments + (size_t)(fld == 0 ? 1 : 4) * N, N * sizeof(double), cudaMemcpyHostToDevice,
+                              s->stream));
+        CK(s, s->kt->from_double(s->stream, prev, acc, (long long)N));
       } else {
-        CK(s, cudaMemcpyAsync(s->phi[2], s->phi[0], N * s->kt->tbytes, cudaMemcpyDeviceToDevice, s->stream));
+        CK(s, cudaMemcpyAsync(prev, mom[fld], N * s->kt->tbytes, cudaMemcpyDeviceToDevice, s->stream));
       }
     }
     for (int i = 0; i < qs[fld]; ++i) {
@@ -660,21 +664,22 @@ int import_state(lbpf_sim* s, const double* g, const double* h, const double* f,
       if (j < i) continue;
       CK(s, cudaMemcpyAsync(b0, host[fld] + (size_t)i * N, N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
       CK(s, cudaMemcpyAsync(b1, host[fld] + (size_t)j * N, N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-      CK(s, s->kt->pack(s->stream, s->hd, fld, 0, L, i, b0, b1, s->phi[2]));
+      CK(s, s->kt->pack(s->stream, s->hd, fld, 0, L, i, b0, b1, prev));
     }
     CK(s, cudaStreamSynchronize(s->stream));
   }
   return LBPF_OK;
 }
 
-// Export phi^n, phi^{n-1}, U^n, theta^n as FP64 (4 x nsite).
+// Export phi^n, phi^{n-1}, U^n, theta^n, theta^{n-1} as FP64 (5 x nsite).
 int export_moments(lbpf_sim* s, double* out) {
   int rc = ensure_tmp(s);
   if (rc) return rc;
   const size_t N = (size_t)s->nsite;
-  const void* src[4] = {s->phi[s6_of(s) % 3], s->phi[(s6_of(s) + 2) % 3], s->U[par_of(s)],
-                        s->lat.q_theta ? s->th[par_of(s)] : nullptr};
-  for (int k = 0; k < 4; ++k) {
+  const bool th = s->lat.q_theta != 0;
+  const void* src[5] = {s->phi[s6_of(s) % 3], s->phi[(s6_of(s) + 2) % 3], s->U[par_of(s)],
+                        th ? s->th[s6_of(s) % 3] : nullptr, th ? s->th[(s6_of(s) + 2) % 3] : nullptr};
+  for (int k = 0; k < 5; ++k) {
     if (!src[k]) {
       for (size_t i = 0; i < N; ++i) out[k * N + i] = s->theta0;
       continue;
@@ -703,14 +708,15 @@ int lbpf_get_state(lbpf_sim* s, double* g, double* h, double* f) {
   double* b1 = s->d_tmp + 2 * N;
   double* host[3] = {g, h, f};
   const int qs[3] = {s->lat.q_phi, s->lat.q_u, s->lat.q_theta};
-  const void* phi_prev = s->phi[(s6_of(s) + 2) % 3];
+  // codec references of g and f: phi^{n-1}, theta^{n-1}
+  const void* prev[3] = {s->phi[(s6_of(s) + 2) % 3], nullptr, s->th[(s6_of(s) + 2) % 3]};
   for (int fld = 0; fld < 3; ++fld) {
     if (!qs[fld] || !host[fld]) continue;
     const LatRT L = make_lat_rt(qs[fld]);
     for (int i = 0; i < qs[fld]; ++i) {
       const int j = L.opp[i];
       if (j < i) continue;
-      CK(s, s->kt->unpack(s->stream, s->hd, fld, par_of(s), L, i, b0, b1, phi_prev));
+      CK(s, s->kt->unpack(s->stream, s->hd, fld, par_of(s), L, i, b0, b1, prev[fld]));
       CK(s, cudaMemcpyAsync(host[fld] + (size_t)i * N, b0, N * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
       if (j != i)
         CK(s, cudaMemcpyAsync(host[fld] + (size_t)j * N, b1, N * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
@@ -747,7 +753,8 @@ int lbpf_autotune(lbpf_sim* s, int32_t steps, double* best_ms) {
     if (qs[f]) live.push_back({s->pop[par][f], (size_t)qs[f] * N * s->kt->sbytes});
   for (int l = 0; l < 3; ++l) live.push_back({s->phi[l], N * s->kt->tbytes});
   live.push_back({s->U[par], N * s->kt->tbytes});
-  if (s->th[par]) live.push_back({s->th[par], N * s->kt->tbytes});
+  for (int l = 0; l < 3; ++l)
+    if (s->th[l]) live.push_back({s->th[l], N * s->kt->tbytes});
   std::vector<void*> snap(live.size(), nullptr);
   for (size_t k = 0; k < live.size(); ++k) {
     if (cudaMalloc(&snap[k], live[k].second) != cudaSuccess) {
@@ -824,13 +831,13 @@ int lbpf_save(lbpf_sim* s, const char* path) {
   for (int f = 0; f < 3; ++f) buf[f].resize((size_t)qs[f] * N);
   int rc = lbpf_get_state(s, buf[0].data(), buf[1].data(), qs[2] ? buf[2].data() : nullptr);
   if (rc) return rc;
-  std::vector<double> mom(4 * N);
+  std::vector<double> mom(5 * N);
   if ((rc = export_moments(s, mom.data()))) return rc;
   FILE* fp = fopen(path, "wb");
   if (!fp) return LBPF_EINVAL;
   CkptHeader hdr{};
-  memcpy(hdr.magic, "LBPFCKP2", 8);
-  hdr.version = 2;
+  memcpy(hdr.magic, "LBPFCKP3", 8);
+  hdr.version = 3;
   hdr.grid = s->g;
   hdr.lat = s->lat;
   hdr.params = s->p;
@@ -851,7 +858,7 @@ int lbpf_load(lbpf_sim* s, const char* path) {
   FILE* fp = fopen(path, "rb");
   if (!fp) return LBPF_EINVAL;
   CkptHeader hdr{};
-  if (fread(&hdr, sizeof(hdr), 1, fp) != 1 || memcmp(hdr.magic, "LBPFCKP2", 8) != 0 ||
+  if (fread(&hdr, sizeof(hdr), 1, fp) != 1 || memcmp(hdr.magic, "LBPFCKP3", 8) != 0 ||
       memcmp(&hdr.grid, &s->g, sizeof(lbpf_grid)) != 0 || memcmp(&hdr.lat, &s->lat, sizeof(lbpf_lattice)) != 0) {
     fclose(fp);
     return LBPF_EINVAL;
@@ -864,7 +871,7 @@ int lbpf_load(lbpf_sim* s, const char* path) {
     buf[f].resize((size_t)qs[f] * N);
     if (qs[f]) ok = fread(buf[f].data(), sizeof(double), buf[f].size(), fp) == buf[f].size();
   }
-  std::vector<double> mom(4 * N);
+  std::vector<double> mom(5 * N);
   if (ok) ok = fread(mom.data(), sizeof(double), mom.size(), fp) == mom.size();
   fclose(fp);
   if (!ok) return LBPF_EINVAL;

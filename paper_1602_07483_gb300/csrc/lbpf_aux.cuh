@@ -132,11 +132,11 @@ __global__ void k_to_double(double* __restrict__ out, const T* __restrict__ in, 
 }
 
 // Post-streaming populations (host convention) -> pull layout, for the pair
-// (i, j = opp(i)).  `shift_w` is w_i times the codec shift of this field, or
-// for field 0 the codec shift comes from phi_prev (w_i phi_prev(x)).
+// (i, j = opp(i)).  FP16/BF16 codec shift of the value stored at x: w_i prev(x) for g and f
+// (prev = phi^{n-1}, theta^{n-1}), the constant w_i U0 for h.
 template <typename S>
 __global__ void k_pack(SimDev sd, int field, int par, LatRT L, int i, const double* __restrict__ gi,
-                       const double* __restrict__ gj, const typename Codec<S>::T* __restrict__ phi_prev) {
+                       const double* __restrict__ gj, const typename Codec<S>::T* __restrict__ prev) {
   using C = Codec<S>;
   using T = typename C::T;
   const int nx = sd.nx, ny = sd.ny, nz = sd.nz;
@@ -150,16 +150,16 @@ __global__ void k_pack(SimDev sd, int field, int par, LatRT L, int i, const doub
     const int x = (int)(s % nx);
     const int y = (int)((s / nx) % ny);
     const int z = (int)(s / ((long long)nx * ny));
-    const T sh = C::shifted ? (field == 0 ? wi * phi_prev[s] : wi * cshift) : T(0);
+    const T sh = C::shifted ? (field != 1 ? wi * prev[s] : wi * cshift) : T(0);
     {
       const int a = x + L.e[i][0], b = y + L.e[i][1], c = z + L.e[i][2];
       const double v = in_dom(a, b, c, nx, ny, nz) ? gi[((long long)c * ny + b) * nx + a] : gj[s];
-      A[(long long)i * n + s] = C::enc((T)v, sh, scale);
+      A[(long long)i * n + s] = C::enc64(v, (double)sh, (double)scale);
     }
     if (j != i) {
       const int a = x + L.e[j][0], b = y + L.e[j][1], c = z + L.e[j][2];
       const double v = in_dom(a, b, c, nx, ny, nz) ? gj[((long long)c * ny + b) * nx + a] : gi[s];
-      A[(long long)j * n + s] = C::enc((T)v, sh, scale);
+      A[(long long)j * n + s] = C::enc64(v, (double)sh, (double)scale);
     }
   }
 }
@@ -167,7 +167,7 @@ __global__ void k_pack(SimDev sd, int field, int par, LatRT L, int i, const doub
 // Pull layout -> post-streaming populations for the pair (i, opp(i)).
 template <typename S>
 __global__ void k_unpack(SimDev sd, int field, int par, LatRT L, int i, double* __restrict__ gi,
-                         double* __restrict__ gj, const typename Codec<S>::T* __restrict__ phi_prev) {
+                         double* __restrict__ gj, const typename Codec<S>::T* __restrict__ prev) {
   using C = Codec<S>;
   using T = typename C::T;
   const int nx = sd.nx, ny = sd.ny, nz = sd.nz;
@@ -186,8 +186,8 @@ __global__ void k_unpack(SimDev sd, int field, int par, LatRT L, int i, double* 
       const int a = x - L.e[d][0], b = y - L.e[d][1], c = z - L.e[d][2];
       const bool ins = in_dom(a, b, c, nx, ny, nz);
       const long long src = ins ? ((long long)c * ny + b) * nx + a : s;
-      const T sh = C::shifted ? (field == 0 ? wi * phi_prev[src] : wi * cshift) : T(0);
-      const double v = (double)C::dec(A[(long long)(ins ? d : o) * n + src], sh, isc);
+      const T sh = C::shifted ? (field != 1 ? wi * prev[src] : wi * cshift) : T(0);
+      const double v = C::dec64(A[(long long)(ins ? d : o) * n + src], (double)sh, (double)isc);
       (pass == 0 ? gi : gj)[s] = v;
     }
   }

@@ -235,6 +235,9 @@ template <typename S>
 struct Codec;
 // raw(s) / pack(v): the stored number itself as T and back (round to nearest), for
 // arithmetic done directly in the scaled units (f - shift) * scale.
+// dec64 / enc64: the same codec evaluated in FP64 for state import and export: with a
+// power-of-two scale, s / scale + shift is exact in FP64, so export then import returns
+// every stored number unchanged.
 template <>
 struct Codec<double> {
   using T = double;
@@ -243,6 +246,8 @@ struct Codec<double> {
   __device__ static __forceinline__ double enc(T v, T, T) { return v; }
   __device__ static __forceinline__ T raw(double s) { return s; }
   __device__ static __forceinline__ double pack(T v) { return v; }
+  __device__ static __forceinline__ double dec64(double s, double, double) { return s; }
+  __device__ static __forceinline__ double enc64(double v, double, double) { return v; }
 };
 template <>
 struct Codec<float> {
@@ -252,6 +257,8 @@ struct Codec<float> {
   __device__ static __forceinline__ float enc(T v, T, T) { return v; }
   __device__ static __forceinline__ T raw(float s) { return s; }
   __device__ static __forceinline__ float pack(T v) { return v; }
+  __device__ static __forceinline__ double dec64(float s, double, double) { return (double)s; }
+  __device__ static __forceinline__ float enc64(double v, double, double) { return (float)v; }
 };
 template <>
 struct Codec<__half> {
@@ -263,6 +270,12 @@ struct Codec<__half> {
   __device__ static __forceinline__ __half enc(T v, T shift, T scale) { return __float2half_rn((v - shift) * scale); }
   __device__ static __forceinline__ T raw(__half s) { return __half2float(s); }
   __device__ static __forceinline__ __half pack(T v) { return __float2half_rn(v); }
+  __device__ static __forceinline__ double dec64(__half s, double shift, double inv_scale) {
+    return (double)__half2float(s) * inv_scale + shift;
+  }
+  __device__ static __forceinline__ __half enc64(double v, double shift, double scale) {
+    return __double2half((v - shift) * scale);
+  }
 };
 template <>
 struct Codec<__nv_bfloat16> {
@@ -276,6 +289,12 @@ struct Codec<__nv_bfloat16> {
   }
   __device__ static __forceinline__ T raw(__nv_bfloat16 s) { return __bfloat162float(s); }
   __device__ static __forceinline__ __nv_bfloat16 pack(T v) { return __float2bfloat16_rn(v); }
+  __device__ static __forceinline__ double dec64(__nv_bfloat16 s, double shift, double inv_scale) {
+    return (double)__bfloat162float(s) * inv_scale + shift;
+  }
+  __device__ static __forceinline__ __nv_bfloat16 enc64(double v, double shift, double scale) {
+    return __double2bfloat16((v - shift) * scale);
+  }
 };
 
 // ---------------------------------------------------------------- descriptors
@@ -286,7 +305,7 @@ struct SimDev {
   void* pop[2][3];  // [buffer][g, h, f] in the storage type, [Q][z][y][x]
   void* phi[3];     // phi levels (compute type); level s%3 is phi^n at step s
   void* U[2];       // U^n at buffer s%2
-  void* th[2];      // theta^n at buffer s%2 (unused when q_theta == 0)
+  void* th[3];      // theta levels (unused when q_theta == 0); level s%3 is theta^n at step s
   double inv2dx;    // 1 / (2 dx)
   double c_eta;     // e^-2 (W0^2/tau0) dt/dx^2: eta_phi = c_eta a_s^2 + 1/2 (Eq. LBE_RelaxationTime)
   double c_N;       // e^-2 (dt/dx) W0^2/tau0: the N term of g^(0) (Eq. Feq_Phase)
@@ -303,7 +322,7 @@ struct SimDev {
   double dt, inv_dt;
   double inv_etaT;  // 1 / eta_theta (Eq. ThermalDiffusivity)
   double theta0;
-  double shift_h, shift_f;       // FP16/BF16 codec: h shifted by w_i U0, f by w_i theta0
+  double shift_h, shift_f;       // FP16/BF16 codec: h shifted by w_i U0; f initially by w_i theta0
   double scale[3], inv_scale[3]; // FP16/BF16 codec scales of g, h, f
 };
 
@@ -467,7 +486,7 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_PHI
   const T* __restrict__ phim = (const T*)sd.phi[(s6 + 2) % 3];
   T* __restrict__ phinew = (T*)sd.phi[(s6 + 1) % 3];
   const T* __restrict__ Un = (const T*)sd.U[par];
-  const T* __restrict__ thn = (const T*)sd.th[par];
+  const T* __restrict__ thn = (const T*)sd.th[s6 % 3];
   const bool has_th = sd.q_theta != 0;
 
   constexpr bool HY = L::has_y;  // false: 2D lattice, one-row blocks without y halo
@@ -758,21 +777,25 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_UTH
   const T* __restrict__ phi1 = (const T*)sd.phi[(s6 + 1) % 3];
   const T* __restrict__ Un = (const T*)sd.U[par];
   T* __restrict__ Unew = (T*)sd.U[par ^ 1];
-  const T* __restrict__ thn = (const T*)sd.th[par];
-  T* __restrict__ thnew = (T*)sd.th[par ^ 1];
+  const T* __restrict__ thn = (const T*)sd.th[s6 % 3];
+  T* __restrict__ thnew = (T*)sd.th[(s6 + 1) % 3];
+  const T* __restrict__ thm = (const T*)sd.th[(s6 + 2) % 3];  // theta^{n-1}: the FP16/BF16 shift of f
 
   constexpr bool HY = LU::has_y;  // false: 2D lattices, one-row blocks without y halo
   const int RW = 34, RS = HY ? RW * (BY + 2) : RW, PS = BY * 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ring = reinterpret_cast<T*>(smem_raw);  // phi^{n+1} [4][BY+2][34]
-  T* sH = ring + 4 * RS;                     // [2][NYU + NYT][BY][32]
+  // FP16/BF16 with theta evolving: theta^{n-1} [4][BY+2][34], the shift of each stored f
+  constexpr bool TSH = C::shifted && QT > 0;
+  T* ringt = ring + 4 * RS;
+  T* sH = ring + (TSH ? 8 : 4) * RS;         // [2][NYU + NYT][BY][32]
   constexpr int NYA = NYU + NYT;
 
   const T inv2dx = (T)sd.inv2dx, k = (T)sd.k, inv_etaU = (T)sd.inv_etaU, c_J = (T)sd.c_J;
   const T D_dx2 = (T)sd.D_dx2, D = (T)sd.D, at_amp = (T)sd.at_amp, inv_dt = (T)sd.inv_dt, dt = (T)sd.dt;
   const T g2min = (T)sd.grad2_min, inv_etaT = (T)sd.inv_etaT;
   const T sh_h = (T)sd.shift_h, sc_h = (T)sd.scale[1], isc_h = (T)sd.inv_scale[1];
-  const T sh_f = (T)sd.shift_f, sc_f = (T)sd.scale[2], isc_f = (T)sd.inv_scale[2];
+  const T sc_f = (T)sd.scale[2], isc_f = (T)sd.inv_scale[2];
   const bool at_on = sd.antitrapping != 0;
   const T opk = T(1) + k, omk = T(1) - k;
 
@@ -784,10 +807,17 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_UTH
     for (int z = zlo - 1; z <= zlo + 1; ++z) {
       a.fetch(rm, phi1, z, nz, plane);
       a.store(rm, ring + slot4(z) * RS, tid, nthr);
+      if (TSH) {
+        a.fetch(rm, thm, z, nz, plane);
+        a.store(rm, ringt + slot4(z) * RS, tid, nthr);
+      }
     }
   }
-  RingRegs<T> pf;
-  if (zlo + 2 <= zhi + 1) pf.fetch(rm, phi1, zlo + 2, nz, plane);
+  RingRegs<T> pf, pft;
+  if (zlo + 2 <= zhi + 1) {
+    pf.fetch(rm, phi1, zlo + 2, nz, plane);
+    if (TSH) pft.fetch(rm, thm, zlo + 2, nz, plane);
+  }
   T u0A = 0, u1A = 0, u2A = 0, t0A = 0, t1A = 0, t2A = 0;
   int buf = 0;
   __syncthreads();
@@ -831,6 +861,8 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_UTH
             const int ex = LT::ex(i), ey = LT::ey(i), ez = LT::ez(i);
             if (!row_needs(ey)) continue;
             fs[i] = C::raw(ldro(fin + ((unsigned)i * NS + site - (unsigned)(ez * (int)plane + ey * nx + ex))));
+            if (TSH)  // stored units with the source's shift: F + S w theta^{n-1}(src)
+              fs[i] = fma(rmul(sc_f, (T)LT::w(i)), (ringt + slot4(zc - ez) * RS)[rc - ey * RW - ex], fs[i]);
           }
         } else {
 #pragma unroll
@@ -852,6 +884,9 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_UTH
             const unsigned src = inside ? site - (unsigned)(ez * (int)plane + ey * nx + ex) : site;
             const int ii = inside ? i : LT::opp(i);
             fs[i] = C::raw(ldro(fin + ((unsigned)ii * NS + src)));
+            if (TSH)
+              fs[i] = fma(rmul(sc_f, (T)LT::w(i)), (ringt + slot4(inside ? sz : zc) * RS)[inside ? rc - ey * RW - ex : rc],
+                          fs[i]);
           }
         }
         // phi^{n+1} at the node and its six neighbours (mirror ghosts)
@@ -949,8 +984,11 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_UTH
           // f* = f (1 - 1/eta_T) + w (theta/eta_T + Q_theta dt) with Q_theta dt = dphi / 2
           const T omT = T(1) - inv_etaT;
           T kT = radd(rmul(inv_etaT, th), rmul(T(0.5), dphi));
-          // FP16/BF16: F* = F (1 - 1/eta_T) + w S (theta/eta_T + dphi/2 - theta0/eta_T) in stored units
-          if (C::shifted) kT = rmul(sc_f, radd(kT, -rmul(sh_f, inv_etaT)));
+          // FP16/BF16: f is stored as F = (f - w theta_ref) S with theta_ref the theta of the
+          // storing node one step earlier; with F' = F + S w theta^{n-1}(src) (pulled) and
+          // F* = (f* - w theta^n) S the update is F* = F' (1 - 1/eta_T) + w S (dphi/2 - theta^n (1 - 1/eta_T)),
+          // and the value gathered for theta^{n+1} is F* + S w theta^n
+          if (C::shifted) kT = rmul(sc_f, radd(rmul(T(0.5), dphi), -rmul(th, omT)));
 #pragma unroll
           for (int i = 0; i < QT; ++i) {
             const int ey = LT::ey(i);
@@ -959,7 +997,7 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_UTH
             const T f = fma(fs[i], omT, rmul(wi, kT));
             const auto enc = C::pack(f);
             if (store) fout[(unsigned)i * NS + site] = enc;
-            fs[i] = C::raw(enc);
+            fs[i] = C::shifted ? radd(C::raw(enc), rmul(rmul(sc_f, wi), th)) : C::raw(enc);
             if (ey != 0) sFb[YT::slot(i) * PS + ly * 32 + tx] = fs[i];
           }
         }
@@ -1037,8 +1075,14 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_UTH
     else if (ty == 0) collide_row(std::integral_constant<int, 1>{}, u0A, u1A, u2A, t0A, t1A, t2A);
     else if (ty == BY - 1) collide_row(std::integral_constant<int, 2>{}, u0A, u1A, u2A, t0A, t1A, t2A);
     else collide_row(std::integral_constant<int, 0>{}, u0A, u1A, u2A, t0A, t1A, t2A);
-    if (zc + 2 <= zhi + 1) pf.store(rm, ring + slot4(zc + 2) * RS, tid, nthr);
-    if (zc + 3 <= zhi + 1) pf.fetch(rm, phi1, zc + 3, nz, plane);
+    if (zc + 2 <= zhi + 1) {
+      pf.store(rm, ring + slot4(zc + 2) * RS, tid, nthr);
+      if (TSH) pft.store(rm, ringt + slot4(zc + 2) * RS, tid, nthr);
+    }
+    if (zc + 3 <= zhi + 1) {
+      pf.fetch(rm, phi1, zc + 3, nz, plane);
+      if (TSH) pft.fetch(rm, thm, zc + 3, nz, plane);
+    }
     __syncthreads();
     auto gather_row = [&](const int r, T& u0, T& u1, T& u2, T& t0, T& t1, T& t2) {
       const int ly = ty;
@@ -1100,7 +1144,7 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_UTH
         // FP16/BF16: the gathered sums are in stored units; the shifts w_i U0 (w_i theta0)
         // of the populations arriving at a node add up to U0 (theta0)
         auto mU = [&](T a) { return C::shifted ? fma(a, isc_h, sh_h) : a; };
-        auto mT = [&](T a) { return C::shifted ? fma(a, isc_f, sh_f) : a; };
+        auto mT = [&](T a) { return C::shifted ? rmul(a, isc_f) : a; };
         if (zw >= it.z0 && zw < it.z1 && zw >= 0) {
           const unsigned sw = ((unsigned)zw * ny + y) * (unsigned)nx + x;
           Unew[sw] = mU(u0);

@@ -26,10 +26,12 @@ struct KernelTable {
                              double c, void* out);
   cudaError_t (*init_pop)(cudaStream_t, const SimDev& sd, const LatRT& Lp, const LatRT& Lu, const LatRT& Lt,
                           const void* phi0, double U0, double theta0);
+  // `prev`: the previous level of the field's moment (phi^{n-1} for g, theta^{n-1} for f), the
+  // FP16/BF16 codec shift of those fields
   cudaError_t (*pack)(cudaStream_t, const SimDev& sd, int field, int par, const LatRT& L, int i, const double* gi,
-                      const double* gj, const void* phi_prev);
+                      const double* gj, const void* prev);
   cudaError_t (*unpack)(cudaStream_t, const SimDev& sd, int field, int par, const LatRT& L, int i, double* gi,
-                        double* gj, const void* phi_prev);
+                        double* gj, const void* prev);
   cudaError_t (*to_double)(cudaStream_t, double* out, const void* in, long long n);
   cudaError_t (*from_double)(cudaStream_t, void* out, const double* in, long long n);
   cudaError_t (*sums)(cudaStream_t, const void* phi, const void* U, const void* th, double theta0, double k,
@@ -67,14 +69,15 @@ inline int ny_count(int q) {
 }
 
 // shared-memory bytes of the step kernels for a block of 32 x by threads: four ring planes of (by+2) x 34 scalars (eight with the
-// FP16/BF16 codec in k_phi) and a double-buffered plane of the e_y != 0 populations
+// FP16/BF16 codec: phi^{n-1} in k_phi, theta^{n-1} in k_uth when theta evolves) and a double-buffered plane of the e_y != 0
+// populations
 inline size_t phi_smem_bytes(const KernelTable& t, int qp, int by) {
   const size_t rs = 34u * (size_t)(by + 2);
   return ((t.shifted ? 8 : 4) * rs + 2 * (size_t)ny_count(qp) * 32u * by) * t.tbytes;
 }
 inline size_t uth_smem_bytes(const KernelTable& t, int qu, int qt, int by) {
   const size_t rs = 34u * (size_t)(by + 2);
-  return (4 * rs + 2 * (size_t)(ny_count(qu) + ny_count(qt)) * 32u * by) * t.tbytes;
+  return ((t.shifted && qt ? 8 : 4) * rs + 2 * (size_t)(ny_count(qu) + ny_count(qt)) * 32u * by) * t.tbytes;
 }
 
 }  // namespace lbpf

@@ -45,13 +45,13 @@ struct AuxImpl {
     return cudaGetLastError();
   }
   static cudaError_t pack(cudaStream_t st, const SimDev& sd, int field, int par, const LatRT& L, int i,
-                          const double* gi, const double* gj, const void* phi_prev) {
-    k_pack<S><<<aux_blocks(sd.nsite), AUX_THREADS, 0, st>>>(sd, field, par, L, i, gi, gj, (const T*)phi_prev);
+                          const double* gi, const double* gj, const void* prev) {
+    k_pack<S><<<aux_blocks(sd.nsite), AUX_THREADS, 0, st>>>(sd, field, par, L, i, gi, gj, (const T*)prev);
     return cudaGetLastError();
   }
   static cudaError_t unpack(cudaStream_t st, const SimDev& sd, int field, int par, const LatRT& L, int i, double* gi,
-                            double* gj, const void* phi_prev) {
-    k_unpack<S><<<aux_blocks(sd.nsite), AUX_THREADS, 0, st>>>(sd, field, par, L, i, gi, gj, (const T*)phi_prev);
+                            double* gj, const void* prev) {
+    k_unpack<S><<<aux_blocks(sd.nsite), AUX_THREADS, 0, st>>>(sd, field, par, L, i, gi, gj, (const T*)prev);
     return cudaGetLastError();
   }
   static cudaError_t to_double(cudaStream_t st, double* out, const void* in, long long n) {

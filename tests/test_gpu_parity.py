@@ -342,8 +342,11 @@ def test_batch_set_tiling_rejects_bad_values():
     batch.close()
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
 def test_checkpoint_round_trip_bitwise(storage):
+    """Save, run on, reload, run the same steps again: bit for bit in every storage type
+    (FP16 populations go through FP64 in the file, where decoding and re-encoding with a
+    power-of-two scale is exact)."""
     w = workloads.coupled_dendrite(n=24)
     a = lbpf.sim_from_workload(w, storage=storage)
     a.step(20)
