@@ -187,10 +187,13 @@ def test_paper_2d_tip_velocity_f64(vp_f64):
             assert abs(hist[round(t, 6)] - ora[round(t, 6)]) < 1e-6, t
 
 
-def test_paper_2d_tip_velocity_f32(vp_f64):
-    """FP32 storage and arithmetic over the 37,500 steps: V_p within 1 % of FP64.  (FP16
-    storage is not held to this bound here: with dt = 0.008 the per-step increments of the
-    populations fall below its resolution; the experiments report its deviation.)"""
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_paper_2d_tip_velocity_low_precision(vp_f64, storage):
+    """FP32, FP16 and BF16 storage (FP32 arithmetic) over the 37,500 steps: V_p(300) within
+    1 % of FP64.  At dt = 0.008 theta changes little per step near the interface, so the
+    half-precision codecs hold the bound only because f is stored as its deviation from
+    w_i theta^{n-1} of the storing node (a constant shift w_i theta0 gave FP16 -4.5 % and
+    lost the tip in BF16)."""
     w, ref = vp_f64
-    _, hist = _vp_history("f32")
+    _, hist = _vp_history(storage)
     assert abs(_vp(w, hist, 300.0) / _vp(w, ref, 300.0) - 1) < 0.01
