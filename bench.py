@@ -233,6 +233,7 @@ def run_own(args):
 
     sim = lbpf.Sim(w.grid, w.lattices, storage=args.storage, stream=st.cuda_stream, **w.params)
     sim.init_seed(w.centres, w.radii, w.U0, w.theta0)
+    sim.set_schedule(args.schedule)
     if args.autotune:
         sim.autotune(steps=2)
     by, zchunk = sim.get_tiling()
@@ -271,6 +272,8 @@ def run_own(args):
     uth_ms = ms_uth / args.steps
     phi_ms = ms_phi / args.steps
     dom = ("k_uth", bytes_uth, uth_ms) if ms_uth >= ms_phi else ("k_phi", bytes_phi, phi_ms)
+    if args.schedule == "one_launch":  # one kernel per step: its time is the phase-field entry
+        dom = ("k_step", bytes_uth + bytes_phi, phi_ms)
     achieved = dom[1] / (dom[2] * 1e-3) / 1e9
     traffic = None
     tr_path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -335,16 +338,19 @@ def run_own(args):
                        "seeds": len(w.radii),
                        "l2": "inputs larger than L2 (%.1f GB of populations)" % (
                            2 * s_bytes * (q_phi + q_u + q_t) * sites / 1e9),
-                       "tiling": {"block": [32, by], "zchunk": zchunk}, "parallelism": "replicas x%d" % world},
+                       "tiling": {"block": [32, by], "zchunk": zchunk}, "schedule": args.schedule,
+                       "parallelism": "replicas x%d" % world},
             "roofline": {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic, "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
                          "alg_bytes_per_launch": dom[1], "ms_per_launch": dom[2],
-                         "phi_kernel": {"ms": phi_ms, "GBps": bytes_phi / (phi_ms * 1e-3) / 1e9},
-                         "uth_kernel": {"ms": uth_ms, "GBps": bytes_uth / (uth_ms * 1e-3) / 1e9},
+                         "phi_kernel": ({"ms": phi_ms, "GBps": bytes_phi / (phi_ms * 1e-3) / 1e9}
+                                        if args.schedule == "two_kernels" else None),
+                         "uth_kernel": ({"ms": uth_ms, "GBps": bytes_uth / (uth_ms * 1e-3) / 1e9}
+                                        if args.schedule == "two_kernels" else None),
                          "step_alg_GBps": step_alg, "step_frac": step_alg / hbm},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": (1 if args.schedule == "one_launch" else 2) * args.steps,
             "clocks": clk,
             "developed": developed,
             "sums_ms": sums_ms,
@@ -420,7 +426,7 @@ def run_variants(args, st):
 def run_sweep(st, hbm, steps=60, base_steps=12):
     """The batched parameter sweep: 64 simulations with edges from {48, 64, 80, 96}, Delta, eps
     and k drawn by default_rng(11), FP16 storage, advanced together by one library-owned batch
-    (graph-replayed steps, CUDA events on the batch stream); then the same simulations one by one
+    (tiling autotuned, graph-replayed steps, CUDA events on the batch stream); then the same simulations one by one
     in plain FP64.  Algorithmic bytes: 2 x 2 B x 38 populations = 152 B per FP16 site-update."""
     import numpy as np
     import torch
@@ -428,6 +434,8 @@ def run_sweep(st, hbm, steps=60, base_steps=12):
     ws = workloads.batch_sweep(count=64, storage="f16")
     sites = sum(w.sites for w in ws)
     b = lbpf.batch_from_workloads(ws, stream=st.cuda_stream)
+    b.autotune(steps=12)  # keeps the fastest batch tiling; the members' state is restored
+    tiling = b.get_tiling()
     b.step(6)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -454,7 +462,8 @@ def run_sweep(st, hbm, steps=60, base_steps=12):
         s.close()
     torch.cuda.empty_cache()
     base = sites * base_steps / (t_one * 1e-3) / 1e9
-    return {"sims": len(ws), "sites": sites, "steps": steps, "storage": "f16", "GLUPS": glups,
+    return {"sims": len(ws), "sites": sites, "steps": steps, "storage": "f16",
+            "tiling": {"block_rows": tiling[0], "zchunk": tiling[1]}, "GLUPS": glups,
             "alg_GBps": glups * 152, "hbm_frac": glups * 152 / hbm, "one_by_one_f64_GLUPS": base,
             "one_by_one_f64_steps": base_steps, "speedup": glups / base, "nonfinite_sims": nonfinite}
 
@@ -472,6 +481,8 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16", "f64"],
                     help="population storage (the headline line is f32)")
     ap.add_argument("--autotune", type=int, default=0)
+    ap.add_argument("--schedule", default="two_kernels", choices=["two_kernels", "one_launch"],
+                    help="step schedule (lbpf_set_schedule): the two step kernels, or one persistent launch")
     ap.add_argument("--variants", type=int, default=1)
     ap.add_argument("--developed", type=int, default=2000,
                     help="also time the headline simulation after it has run this many steps (0: skip)")

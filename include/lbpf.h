@@ -47,7 +47,9 @@ extern "C" {
 #define LBPF_EUNSTABLE (-2) /* parameters give a relaxation time <= 1/2 somewhere */
 #define LBPF_ENOMEM (-3)    /* device allocation failed */
 #define LBPF_ENAN (-4)      /* a non-finite value was found in the fields */
-#define LBPF_ECUDA (-6)     /* CUDA runtime error (sticky); -5 is not used */
+#define LBPF_ETIMEOUT (-5)  /* a bounded wait of the one-launch step gave up (sticky; see
+                               lbpf_set_schedule) */
+#define LBPF_ECUDA (-6)     /* CUDA runtime error (sticky) */
 
 /* storage of the distributions; arithmetic is FP64 for LBPF_F64, FP32 otherwise */
 #define LBPF_F64 0
@@ -126,7 +128,9 @@ int lbpf_step(lbpf_sim* sim, int64_t n_steps);
  * events recorded on the handle's stream, and the call returns (synchronously)
  * the summed device time of the phase-field kernels in ms_kernels[0], of the
  * U/theta kernels in ms_kernels[1], and the wall span of the n steps in
- * ms_kernels[2].  Used to measure per-kernel bandwidth. */
+ * ms_kernels[2].  Under the one-launch schedule the whole step is one kernel:
+ * its time is in ms_kernels[0] and ms_kernels[1] is 0.  Used to measure
+ * per-kernel bandwidth. */
 int lbpf_step_timed(lbpf_sim* sim, int64_t n_steps, double ms_kernels[3]);
 
 /* Copy phi, U and/or theta (as selected by mask) of the current step to the
@@ -177,6 +181,30 @@ int lbpf_get_tiling(const lbpf_sim* sim, int32_t* by, int32_t* zchunk);
  * (may be NULL) receives the best time per step.  Synchronous. */
 int lbpf_autotune(lbpf_sim* sim, int32_t steps, double* best_ms);
 
+/* How a step is launched (the order of the work within a step follows Sec. 3.4:
+ * phi first, then U and theta with phi^{n+1}; both schedules give bit-identical results).
+ *   LBPF_SCHED_TWO_KERNELS (default): the phase-field kernel over all tiles, then the
+ *     U/theta kernel over all tiles.
+ *   LBPF_SCHED_ONE_LAUNCH: one persistent kernel per step in which the U/theta tile of a
+ *     region starts as soon as the phase-field tiles that write phi^{n+1} around it are done,
+ *     so that both phases run side by side on the SMs.  Its blocks wait on flags set by
+ *     other blocks of the same launch, in an order that always lets them finish; every wait
+ *     is bounded (about a second), and a wait that gives up makes the handle fail with
+ *     LBPF_ETIMEOUT at the next call that returns data.  Available for FP32, FP16 and BF16
+ *     storage with the lattice triples D3Q19 x D3Q19 x {frozen theta, D3Q7, D3Q19} and
+ *     D2Q9 x D2Q5 x D2Q5 (LBPF_EINVAL otherwise).
+ * Synchronises the handle's stream; the step graph is re-captured at the next step. */
+#define LBPF_SCHED_TWO_KERNELS 0
+#define LBPF_SCHED_ONE_LAUNCH 1
+int lbpf_set_schedule(lbpf_sim* sim, int32_t schedule);
+int lbpf_get_schedule(const lbpf_sim* sim, int32_t* schedule);
+
+/* Diagnostic of the bounded wait the one-launch step uses: one warp waits on a device flag
+ * initialised to `flag_value` for at most `polls` rounds (each about 0.25 us); *seen is 1
+ * when the wait saw the flag set (flag_value != 0), 0 when it gave up.  The device stays
+ * usable either way.  Synchronous (synchronises the device). */
+int lbpf_wait_probe(int32_t flag_value, int32_t polls, int32_t* seen);
+
 int lbpf_destroy(lbpf_sim* sim);
 
 /* Batched stepping: several independent simulations with identical lattices and storage
@@ -210,6 +238,24 @@ int lbpf_batch_step(lbpf_batch* batch, int64_t n_steps);
  * default).  Results do not depend on the tiling.  LBPF_EINVAL for values out of
  * range.  Synchronises the batch stream. */
 int lbpf_batch_set_tiling(lbpf_batch* batch, int32_t by, int32_t zchunk);
+/* The batch's current tiling: block rows and the z-chunk request (0: each member's
+ * default).  Either pointer may be NULL. */
+int lbpf_batch_get_tiling(const lbpf_batch* batch, int32_t* by, int32_t* zchunk);
+/* Times the candidate batch tilings and keeps the fastest, as lbpf_autotune does for
+ * one handle: block rows 4, 6 and 8 with z-chunks of each member's default, 12, 16 and
+ * 24 planes (2D lattices: one-row blocks with chunks of the default, 8, 16 and 32 rows).
+ * Each candidate runs single steps up to the next multiple of 6 steps, 6 warm-up steps,
+ * then `steps` rounded up to a multiple of 6, timed with CUDA events on the batch
+ * stream; every member's state and step count are restored afterwards, so the batch
+ * continues exactly as if the call had not been made (the state is copied on the device:
+ * LBPF_ENOMEM, tiling unchanged, when the copy of all members does not fit).
+ * best_ms (may be NULL): milliseconds per batch step of the tiling kept.  All members
+ * must have taken the same number of steps (LBPF_EINVAL otherwise).  Synchronous. */
+int lbpf_batch_autotune(lbpf_batch* batch, int32_t steps, double* best_ms);
+/* The step schedule of the batched launches, as lbpf_set_schedule for one handle (the
+ * one-launch schedule spans the tiles of all members).  Synchronises the batch stream. */
+int lbpf_batch_set_schedule(lbpf_batch* batch, int32_t schedule);
+int lbpf_batch_get_schedule(const lbpf_batch* batch, int32_t* schedule);
 int lbpf_batch_destroy(lbpf_batch* batch);
 
 /* Largest n_sites that lbpf_field_sums_noalloc accepts (65536 partial sums of

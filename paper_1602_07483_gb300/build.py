@@ -17,8 +17,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "liblbpf.so")
-SOURCES = ["lbpf_api.cu", "kern_f64.cu", "kern_f32.cu", "kern_f16.cu", "kern_bf16.cu", "lbpf_noalloc.cu"]
-HEADERS = ["lbpf_dev.cuh", "lbpf_aux.cuh", "lbpf_table.h", "lbpf_table_impl.cuh"]
+SOURCES = ["lbpf_api.cu", "kern_f64.cu", "kern_f32.cu", "kern_f16.cu", "kern_bf16.cu", "kern_f64_b8.cu",
+           "kern_f32_b8.cu", "kern_f16_b8.cu", "kern_bf16_b8.cu", "kern_step_f32.cu", "kern_step_f16.cu",
+           "kern_step_bf16.cu", "lbpf_noalloc.cu"]
+HEADERS = ["lbpf_dev.cuh", "lbpf_aux.cuh", "lbpf_table.h", "lbpf_table_impl.cuh", "lbpf_plan.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 

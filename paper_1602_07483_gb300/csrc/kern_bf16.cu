@@ -3,7 +3,12 @@
 
 namespace lbpf {
 const KernelTable& table_bf16() {
-  static const KernelTable t = build_table<__nv_bfloat16>();
+  static const KernelTable t = [] {
+    KernelTable k = build_table<__nv_bfloat16>();
+    add_fixed_kernels_bf16(k);
+    add_step_kernels_bf16(k);
+    return k;
+  }();
   return t;
 }
 }  // namespace lbpf

@@ -3,7 +3,12 @@
 
 namespace lbpf {
 const KernelTable& table_f16() {
-  static const KernelTable t = build_table<__half>();
+  static const KernelTable t = [] {
+    KernelTable k = build_table<__half>();
+    add_fixed_kernels_f16(k);
+    add_step_kernels_f16(k);
+    return k;
+  }();
   return t;
 }
 }  // namespace lbpf

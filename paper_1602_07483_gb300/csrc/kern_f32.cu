@@ -3,7 +3,12 @@
 
 namespace lbpf {
 const KernelTable& table_f32() {
-  static const KernelTable t = build_table<float>();
+  static const KernelTable t = [] {
+    KernelTable k = build_table<float>();
+    add_fixed_kernels_f32(k);
+    add_step_kernels_f32(k);
+    return k;
+  }();
   return t;
 }
 }  // namespace lbpf

@@ -3,7 +3,11 @@
 
 namespace lbpf {
 const KernelTable& table_f64() {
-  static const KernelTable t = build_table<double>();
+  static const KernelTable t = [] {
+    KernelTable k = build_table<double>();
+    add_fixed_kernels_f64(k);
+    return k;
+  }();
   return t;
 }
 }  // namespace lbpf

@@ -22,6 +22,9 @@ using namespace lbpf;
 namespace {
 
 constexpr int kGraphSteps = 6;
+#ifndef LBPF_ONE_LAUNCH_LAG_PCT
+#define LBPF_ONE_LAUNCH_LAG_PCT 100  // lag of the one-launch schedule, % of the resident blocks
+#endif
 
 // table slots: phi and U take a moving lattice, theta may also be 0 (frozen)
 int q_index(int q) {
@@ -77,6 +80,21 @@ double min_effective_tau(int kind, double e1, double e2, double c_eta, double* a
 
 }  // namespace
 
+// The one-launch schedule of a tiling (k_step): the ticket order and the dependency lists on
+// the device, the ticket counter and done flags (zeroed before each launch), and the
+// host-visible flag of the bounded waits.
+struct OneLaunch {
+  OneLaunchFn fn = nullptr;   // null: no one-launch kernel for these lattices and storage
+  bool on = false;            // schedule selected (lbpf_set_schedule)
+  int* d_sched = nullptr;     // order[ntickets] | dep_off[nitems + 1] | dep[...]
+  unsigned* d_ctl = nullptr;  // next ticket, then one done flag per work item
+  size_t ctl_bytes = 0;
+  int* h_err = nullptr;       // mapped host memory, written by the device
+  StepSched sc{};
+  int grid = 0;               // resident blocks on the device
+  size_t smem = 0;
+};
+
 struct lbpf_sim {
   lbpf_grid g{};
   lbpf_grid kg{};  // grid as the kernels see it: g, or (nx, 1, ny) for the 2D lattices (paper's y on the z axis)
@@ -109,6 +127,8 @@ struct lbpf_sim {
   double theta0 = 0.0, U0 = 0.0;
   StepLaunch fphi = nullptr, futh = nullptr;
   size_t smem_phi = 0, smem_uth = 0;
+  OneLaunch ol;
+  const int* batch_err = nullptr;  // wait-failure flag of the batch this handle is stepped by
 };
 
 struct lbpf_batch {
@@ -122,8 +142,11 @@ struct lbpf_batch {
   WorkItem* d_items = nullptr;
   int nitems = 0;
   int by = MAX_BLOCK_ROWS;
+  int zchunk = 0;               // z-chunk request of the current tiling (0: each member's default)
   StepLaunch fphi = nullptr, futh = nullptr;
   size_t smem_phi = 0, smem_uth = 0;
+  OneLaunch ol;
+  std::vector<int> zchunks;     // z-chunk of each member under the current tiling
   cudaGraphExec_t gexec = nullptr;
   bool graph_ok = false;
 };
@@ -140,12 +163,6 @@ struct lbpf_batch {
 
 namespace {
 
-void build_items(int sim_index, int nx, int ny, int nz, int by, int zchunk, std::vector<WorkItem>& out) {
-  const int ty = by == 1 ? 1 : by - 2;  // interior rows per block: one-row blocks (2D) have no y halo
-  for (int z0 = 0; z0 < nz; z0 += zchunk)
-    for (int y0 = 0; y0 < ny; y0 += ty)
-      for (int x0 = 0; x0 < nx; x0 += TILE_X) out.push_back(WorkItem{sim_index, x0, y0, z0, std::min(nz, z0 + zchunk)});
-}
 
 // z-chunks of about 32 planes: enough thread blocks for several waves, and the
 // blocks resident at any time work on neighbouring tiles, so the one-node
@@ -179,10 +196,91 @@ int raise_smem_limit(const void* fn, int device) {
   return LBPF_OK;
 }
 
+// The sticky error of a handle; a bounded wait of its one-launch step (or of the batch that
+// steps it) that gave up makes it LBPF_ETIMEOUT.  The flags are in mapped host memory, so
+// this reads them without synchronising (a failure shows at the latest after the next
+// synchronising call).
+int status(lbpf_sim* s) {
+  if (s->sticky == LBPF_OK && ((s->ol.h_err && *(volatile const int*)s->ol.h_err) ||
+                               (s->batch_err && *(volatile const int*)s->batch_err)))
+    s->sticky = LBPF_ETIMEOUT;
+  return s->sticky;
+}
+
+// The bounded wait of the one-launch step on its own: one warp waits for flag[dep[0]] with at
+// most `polls` rounds and writes 1 to *out if it saw the flag set, 0 if it gave up.
+__global__ void k_wait_probe(const unsigned* flag, const int* dep, unsigned polls, int* out) {
+  const bool ok = wait_done(flag, dep, 1, polls);
+  if (threadIdx.x == 0) *out = ok ? 1 : 0;
+}
+
+void free_one_launch(OneLaunch& ol) {
+  if (ol.d_sched) cudaFree(ol.d_sched);
+  if (ol.d_ctl) cudaFree(ol.d_ctl);
+  ol.d_sched = nullptr;
+  ol.d_ctl = nullptr;
+  ol.sc = StepSched{};
+}
+
+// (Re)builds the one-launch schedule of `items` on the device.  Synchronous.
+int setup_one_launch(OneLaunch& ol, const std::vector<WorkItem>& items, const std::vector<TileGeom>& geo, int by,
+                     size_t smem, const void* fn, int device) {
+  free_one_launch(ol);
+  if (!ol.h_err) {
+    if (cudaHostAlloc(&ol.h_err, sizeof(int), cudaHostAllocMapped) != cudaSuccess) {
+      cudaGetLastError();
+      ol.h_err = nullptr;
+      return LBPF_ENOMEM;
+    }
+    *ol.h_err = 0;
+  }
+  int* d_err = nullptr;
+  if (cudaHostGetDevicePointer((void**)&d_err, ol.h_err, 0) != cudaSuccess) return LBPF_ECUDA;
+  int nb = 0, sms = 0;
+  if (raise_smem_limit(fn, device) != LBPF_OK ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 32 * by, smem) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+    return LBPF_ECUDA;
+  if (nb < 1) return LBPF_EINVAL;
+  const int resident = nb * sms;
+  // U/theta tickets trail their last phase-field tile by about one wave of resident blocks,
+  // so that the tiles they wait for have normally finished when they start
+  const int lag = (int)((long long)resident * LBPF_ONE_LAUNCH_LAG_PCT / 100);
+  std::vector<int> order, dep_off, dep;
+  if (!plan_one_launch(items, geo, by, lag, order, dep_off, dep)) return LBPF_EINVAL;
+  const size_t n = items.size();
+  std::vector<int> all;
+  all.reserve(order.size() + dep_off.size() + dep.size());
+  all.insert(all.end(), order.begin(), order.end());
+  all.insert(all.end(), dep_off.begin(), dep_off.end());
+  all.insert(all.end(), dep.begin(), dep.end());
+  ol.ctl_bytes = (n + 1) * sizeof(unsigned);
+  if (cudaMalloc(&ol.d_sched, all.size() * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&ol.d_ctl, ol.ctl_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    free_one_launch(ol);
+    return LBPF_ENOMEM;
+  }
+  if (cudaMemcpy(ol.d_sched, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
+    free_one_launch(ol);
+    return LBPF_ECUDA;
+  }
+  ol.sc.order = ol.d_sched;
+  ol.sc.dep_off = ol.d_sched + order.size();
+  ol.sc.dep = ol.d_sched + order.size() + dep_off.size();
+  ol.sc.ctl = ol.d_ctl;
+  ol.sc.err = d_err;
+  ol.sc.ntickets = (int)order.size();
+  ol.grid = std::min(resident, ol.sc.ntickets);
+  ol.smem = smem;
+  return LBPF_OK;
+}
+
 int set_smem_attrs(lbpf_sim* s) {
   const KernelTable& t = *s->kt;
   const int a = q_index(s->lat.q_phi), b = q_index(s->lat.q_u), c = qt_index(s->lat.q_theta);
-  if (raise_smem_limit(t.phi_fn[a], s->device) || raise_smem_limit(t.uth_fn[b][c], s->device)) {
+  if (raise_smem_limit(t.phi_fn[a][0], s->device) || raise_smem_limit(t.uth_fn[b][c][0], s->device) ||
+      raise_smem_limit(t.phi_fn[a][1], s->device) || raise_smem_limit(t.uth_fn[b][c][1], s->device)) {
     s->sticky = LBPF_ECUDA;
     return LBPF_ECUDA;
   }
@@ -193,6 +291,9 @@ int apply_tiling(lbpf_sim* s, int by, int zchunk) {
   const KernelTable& t = *s->kt;
   if (lattice_is_2d(s->lat.q_phi)) by = 1;  // 2D: one-row blocks, no y halo
   s->by = by;
+  const int v = block_variant(s->lat.q_phi, by);
+  s->fphi = t.phi[q_index(s->lat.q_phi)][v];
+  s->futh = t.uth[q_index(s->lat.q_u)][qt_index(s->lat.q_theta)][v];
   s->zchunk = zchunk > 0 ? zchunk : default_zchunk(s->kg.nx, s->kg.ny, s->kg.nz, by);
   s->smem_phi = phi_smem_bytes(t, s->lat.q_phi, by);
   s->smem_uth = uth_smem_bytes(t, s->lat.q_u, s->lat.q_theta, by);
@@ -209,11 +310,24 @@ int apply_tiling(lbpf_sim* s, int by, int zchunk) {
   if (s->gexec) cudaGraphExecDestroy(s->gexec);
   s->gexec = nullptr;
   s->graph_ok = false;
+  if (s->ol.on) {
+    const int rc = setup_one_launch(s->ol, items, {TileGeom{s->kg.nx, s->kg.ny, s->kg.nz, s->zchunk}}, by,
+                                    step_smem_bytes(t, s->lat.q_phi, s->lat.q_u, s->lat.q_theta, by),
+                                    t.step_fn[q_index(s->lat.q_phi)][q_index(s->lat.q_u)][qt_index(s->lat.q_theta)],
+                                    s->device);
+    if (rc != LBPF_OK) return rc;
+  }
   return set_smem_attrs(s);
 }
 
+// One step: the two kernels, or the one-launch kernel when `ol` is selected.
 int launch_step(cudaStream_t st, StepLaunch fphi, StepLaunch futh, int nitems, int by, size_t smem_phi,
-                size_t smem_uth, const SimDev* dd, const WorkItem* items, int s6) {
+                size_t smem_uth, const SimDev* dd, const WorkItem* items, int s6, const OneLaunch* ol) {
+  if (ol && ol->on) {
+    if (cudaMemsetAsync(ol->d_ctl, 0, ol->ctl_bytes, st) != cudaSuccess) return LBPF_ECUDA;
+    return ol->fn(dim3(ol->grid), dim3(32, by), ol->smem, st, dd, items, ol->sc, s6) == cudaSuccess ? LBPF_OK
+                                                                                                 : LBPF_ECUDA;
+  }
   cudaError_t e = fphi(dim3(nitems), dim3(32, by), smem_phi, st, dd, items, s6);
   if (e != cudaSuccess) return LBPF_ECUDA;
   e = futh(dim3(nitems), dim3(32, by), smem_uth, st, dd, items, s6);
@@ -221,12 +335,13 @@ int launch_step(cudaStream_t st, StepLaunch fphi, StepLaunch futh, int nitems, i
 }
 
 int capture_graph(cudaStream_t st, StepLaunch fphi, StepLaunch futh, int nitems, int by, size_t smem_phi,
-                  size_t smem_uth, const SimDev* dd, const WorkItem* items, cudaGraphExec_t* out) {
+                  size_t smem_uth, const SimDev* dd, const WorkItem* items, const OneLaunch* ol,
+                  cudaGraphExec_t* out) {
   cudaGraph_t graph = nullptr;
   if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LBPF_ECUDA;
   int rc = LBPF_OK;
   for (int s6 = 0; s6 < kGraphSteps && rc == LBPF_OK; ++s6)
-    rc = launch_step(st, fphi, futh, nitems, by, smem_phi, smem_uth, dd, items, s6);
+    rc = launch_step(st, fphi, futh, nitems, by, smem_phi, smem_uth, dd, items, s6, ol);
   cudaError_t e = cudaStreamEndCapture(st, &graph);
   if (rc != LBPF_OK || e != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
@@ -336,6 +451,8 @@ void free_sim(lbpf_sim* s) {
   if (s->h_small) cudaFreeHost(s->h_small);
   if (s->d_tmp) cudaFree(s->d_tmp);
   if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  free_one_launch(s->ol);
+  if (s->ol.h_err) cudaFreeHost(s->ol.h_err);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   delete s;
 }
@@ -360,6 +477,7 @@ const char* lbpf_strerror(int code) {
     case LBPF_ENOMEM: return "device allocation failed";
     case LBPF_ENAN: return "non-finite value in the fields";
     case LBPF_ECUDA: return "CUDA runtime error";
+    case LBPF_ETIMEOUT: return "a bounded wait of the one-launch step gave up; the step's results are invalid";
     default: return "unknown error";
   }
 }
@@ -416,8 +534,7 @@ int lbpf_create(const lbpf_grid* grid, const lbpf_lattice* lattice, const lbpf_p
   for (int b = 0; b < 2; ++b) cudaMemsetAsync(s->U[b], 0, N * s->kt->tbytes, s->stream);
   for (int l = 0; l < 3; ++l)
     if (s->th[l]) cudaMemsetAsync(s->th[l], 0, N * s->kt->tbytes, s->stream);
-  s->fphi = s->kt->phi[q_index(lattice->q_phi)];
-  s->futh = s->kt->uth[q_index(lattice->q_u)][qt_index(lattice->q_theta)];
+  s->ol.fn = s->kt->step[q_index(lattice->q_phi)][q_index(lattice->q_u)][qt_index(lattice->q_theta)];
   // 32 x 8 blocks: two resident blocks per SM at 128 registers per thread
   const int by = lattice_is_2d(lattice->q_phi) ? 1 : std::min(8, std::max(4, grid->ny + 2));
   if ((rc = upload_dev(s)) != LBPF_OK || (rc = apply_tiling(s, by, 0)) != LBPF_OK) {
@@ -440,7 +557,7 @@ int64_t lbpf_steps_done(const lbpf_sim* s) { return s ? s->step_base + s->steps 
 
 int lbpf_init_seed(lbpf_sim* s, int32_t n, const double* centres, const double* radii, double U0, double theta0) {
   if (!s || n < 1 || !centres || !radii) return LBPF_EINVAL;
-  if (s->sticky) return s->sticky;
+  if (status(s)) return s->sticky;
   for (int m = 0; m < n; ++m)
     if (!isfinite(radii[m]) || !isfinite(centres[3 * m]) || !isfinite(centres[3 * m + 1]) ||
         !isfinite(centres[3 * m + 2]))
@@ -478,14 +595,14 @@ int lbpf_init_seed(lbpf_sim* s, int32_t n, const double* centres, const double* 
 
 int lbpf_step(lbpf_sim* s, int64_t n) {
   if (!s || n < 0) return LBPF_EINVAL;
-  if (s->sticky) return s->sticky;
+  if (status(s)) return s->sticky;
   while (n > 0) {
     if (s6_of(s) == 0 && n >= kGraphSteps) {
       if (!s->graph_ok) {
         if (s->gexec) cudaGraphExecDestroy(s->gexec);
         s->gexec = nullptr;
         if (capture_graph(s->stream, s->fphi, s->futh, s->nitems, s->by, s->smem_phi, s->smem_uth, s->dd,
-                          s->d_items, &s->gexec) != LBPF_OK) {
+                          s->d_items, &s->ol, &s->gexec) != LBPF_OK) {
           s->sticky = LBPF_ECUDA;
           return LBPF_ECUDA;
         }
@@ -496,7 +613,7 @@ int lbpf_step(lbpf_sim* s, int64_t n) {
       n -= kGraphSteps;
     } else {
       if (launch_step(s->stream, s->fphi, s->futh, s->nitems, s->by, s->smem_phi, s->smem_uth, s->dd, s->d_items,
-                      s6_of(s)) != LBPF_OK) {
+                      s6_of(s), &s->ol) != LBPF_OK) {
         s->sticky = LBPF_ECUDA;
         return LBPF_ECUDA;
       }
@@ -509,15 +626,25 @@ int lbpf_step(lbpf_sim* s, int64_t n) {
 
 int lbpf_step_timed(lbpf_sim* s, int64_t n, double ms_kernels[3]) {
   if (!s || n < 1 || !ms_kernels) return LBPF_EINVAL;
-  if (s->sticky) return s->sticky;
+  if (status(s)) return s->sticky;
   std::vector<cudaEvent_t> ev((size_t)(2 * n + 1));
   for (auto& e : ev) CK(s, cudaEventCreate(&e));
   CK(s, cudaEventRecord(ev[0], s->stream));
   for (int64_t k = 0; k < n; ++k) {
     const int s6 = s6_of(s);
-    CK(s, s->fphi(dim3(s->nitems), dim3(32, s->by), s->smem_phi, s->stream, s->dd, s->d_items, s6));
-    CK(s, cudaEventRecord(ev[2 * k + 1], s->stream));
-    CK(s, s->futh(dim3(s->nitems), dim3(32, s->by), s->smem_uth, s->stream, s->dd, s->d_items, s6));
+    if (s->ol.on) {
+      // one launch per step: all of its time is counted as the first phase's
+      if (launch_step(s->stream, s->fphi, s->futh, s->nitems, s->by, s->smem_phi, s->smem_uth, s->dd, s->d_items,
+                      s6, &s->ol) != LBPF_OK) {
+        s->sticky = LBPF_ECUDA;
+        return LBPF_ECUDA;
+      }
+      CK(s, cudaEventRecord(ev[2 * k + 1], s->stream));
+    } else {
+      CK(s, s->fphi(dim3(s->nitems), dim3(32, s->by), s->smem_phi, s->stream, s->dd, s->d_items, s6));
+      CK(s, cudaEventRecord(ev[2 * k + 1], s->stream));
+      CK(s, s->futh(dim3(s->nitems), dim3(32, s->by), s->smem_uth, s->stream, s->dd, s->d_items, s6));
+    }
     CK(s, cudaEventRecord(ev[2 * k + 2], s->stream));
     s->steps += 1;
   }
@@ -541,7 +668,7 @@ int lbpf_step_timed(lbpf_sim* s, int64_t n, double ms_kernels[3]) {
 
 int lbpf_read_fields(lbpf_sim* s, uint32_t mask, double* phi, double* U, double* theta) {
   if (!s) return LBPF_EINVAL;
-  if (s->sticky) return s->sticky;
+  if (status(s)) return s->sticky;
   if (((mask & LBPF_PHI) && !phi) || ((mask & LBPF_U) && !U) || ((mask & LBPF_THETA) && !theta)) return LBPF_EINVAL;
   const size_t N = (size_t)s->nsite;
   const void* src[3] = {s->phi[s6_of(s) % 3], s->U[par_of(s)], s->lat.q_theta ? s->th[s6_of(s) % 3] : nullptr};
@@ -567,18 +694,19 @@ int lbpf_read_fields(lbpf_sim* s, uint32_t mask, double* phi, double* U, double*
     }
     CK(s, cudaStreamSynchronize(s->stream));
   }
-  return LBPF_OK;
+  return status(s);
 }
 
 int lbpf_sums(lbpf_sim* s, double out[4]) {
   if (!s || !out) return LBPF_EINVAL;
-  if (s->sticky) return s->sticky;
+  if (status(s)) return s->sticky;
   const void* th = s->lat.q_theta ? s->th[s6_of(s) % 3] : nullptr;
   const int nblk = (int)std::min<long long>(s->npart, std::max<long long>(1, (s->nsite + 255) / 256));
   CK(s, s->kt->sums(s->stream, s->phi[s6_of(s) % 3], s->U[par_of(s)], th, s->theta0, s->p.k, s->nsite, s->d_part,
                     nblk));
   CK(s, cudaMemcpyAsync(s->h_small, s->d_part + 4 * nblk, 4 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   CK(s, cudaStreamSynchronize(s->stream));
+  if (status(s)) return s->sticky;
   bool fin = true;
   for (int c = 0; c < 4; ++c) {
     out[c] = s->h_small[c];
@@ -589,7 +717,7 @@ int lbpf_sums(lbpf_sim* s, double out[4]) {
 
 int lbpf_tip(lbpf_sim* s, int32_t axis, const double centre_lu[3], double* x_tip, double* rho) {
   if (!s || !centre_lu || !x_tip) return LBPF_EINVAL;
-  if (s->sticky) return s->sticky;
+  if (status(s)) return s->sticky;
   const bool d2 = lattice_is_2d(s->lat.q_phi);
   if (axis < 0 || axis > (d2 ? 1 : 2)) return LBPF_EINVAL;
   // the scan starts at the node nearest to the centre
@@ -694,13 +822,13 @@ int export_moments(lbpf_sim* s, double* out) {
 
 int lbpf_set_state(lbpf_sim* s, const double* g, const double* h, const double* f, double theta0) {
   if (!s || !g || !h || (s->lat.q_theta && !f)) return LBPF_EINVAL;
-  if (s->sticky) return s->sticky;
+  if (status(s)) return s->sticky;
   return import_state(s, g, h, f, theta0, nullptr);
 }
 
 int lbpf_get_state(lbpf_sim* s, double* g, double* h, double* f) {
   if (!s) return LBPF_EINVAL;
-  if (s->sticky) return s->sticky;
+  if (status(s)) return s->sticky;
   int rc = ensure_tmp(s);
   if (rc) return rc;
   const size_t N = (size_t)s->nsite;
@@ -728,7 +856,7 @@ int lbpf_get_state(lbpf_sim* s, double* g, double* h, double* f) {
 
 int lbpf_set_tiling(lbpf_sim* s, int32_t by, int32_t zchunk) {
   if (!s || by < 0 || zchunk < 0 || (by && (by < 4 || by > MAX_BLOCK_ROWS))) return LBPF_EINVAL;
-  if (s->sticky) return s->sticky;
+  if (status(s)) return s->sticky;
   CK(s, cudaStreamSynchronize(s->stream));
   return apply_tiling(s, by ? by : s->by, zchunk ? zchunk : (by ? 0 : s->zchunk));
 }
@@ -740,14 +868,58 @@ int lbpf_get_tiling(const lbpf_sim* s, int32_t* by, int32_t* zchunk) {
   return LBPF_OK;
 }
 
-int lbpf_autotune(lbpf_sim* s, int32_t steps, double* best_ms) {
-  if (!s || steps < 1) return LBPF_EINVAL;
-  if (s->sticky) return s->sticky;
+int lbpf_set_schedule(lbpf_sim* s, int32_t schedule) {
+  if (!s || (schedule != LBPF_SCHED_TWO_KERNELS && schedule != LBPF_SCHED_ONE_LAUNCH)) return LBPF_EINVAL;
+  if (status(s)) return s->sticky;
+  if (schedule == LBPF_SCHED_ONE_LAUNCH && !s->ol.fn) return LBPF_EINVAL;
   CK(s, cudaStreamSynchronize(s->stream));
-  // snapshot of the current state: populations at the current buffer, all phi levels, U, theta
+  const bool was = s->ol.on;
+  s->ol.on = schedule == LBPF_SCHED_ONE_LAUNCH;
+  const int rc = apply_tiling(s, s->by, s->zchunk);
+  if (rc != LBPF_OK) {
+    s->ol.on = was;
+    free_one_launch(s->ol);
+    apply_tiling(s, s->by, s->zchunk);
+  }
+  if (!s->ol.on) free_one_launch(s->ol);
+  return rc;
+}
+
+int lbpf_get_schedule(const lbpf_sim* s, int32_t* schedule) {
+  if (!s || !schedule) return LBPF_EINVAL;
+  *schedule = s->ol.on ? LBPF_SCHED_ONE_LAUNCH : LBPF_SCHED_TWO_KERNELS;
+  return LBPF_OK;
+}
+
+int lbpf_wait_probe(int32_t flag_value, int32_t polls, int32_t* seen) {
+  if (!seen || polls < 1) return LBPF_EINVAL;
+  unsigned* d = nullptr;  // flag, dependency index 0, result
+  if (cudaMalloc(&d, 3 * sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    return LBPF_ENOMEM;
+  }
+  const unsigned h[3] = {(unsigned)flag_value, 0u, 2u};
+  int out = 2;
+  bool ok = cudaMemcpy(d, h, sizeof(h), cudaMemcpyHostToDevice) == cudaSuccess;
+  if (ok) {
+    k_wait_probe<<<1, 32>>>(d, (const int*)(d + 1), (unsigned)polls, (int*)(d + 2));
+    ok = cudaGetLastError() == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess &&
+         cudaMemcpy(&out, d + 2, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+  }
+  cudaFree(d);
+  if (!ok || (out != 0 && out != 1)) return LBPF_ECUDA;
+  *seen = out;
+  return LBPF_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// The device state the next step reads: populations and U at the current buffer parity and
+// every phi and theta level.  A copy of these restores the handle exactly (with its step count).
+void live_state(const lbpf_sim* s, std::vector<std::pair<void*, size_t>>& live) {
   const size_t N = (size_t)s->nsite;
   const int qs[3] = {s->lat.q_phi, s->lat.q_u, s->lat.q_theta};
-  std::vector<std::pair<void*, size_t>> live;
   const int par = par_of(s);
   for (int f = 0; f < 3; ++f)
     if (qs[f]) live.push_back({s->pop[par][f], (size_t)qs[f] * N * s->kt->sbytes});
@@ -755,14 +927,55 @@ int lbpf_autotune(lbpf_sim* s, int32_t steps, double* best_ms) {
   live.push_back({s->U[par], N * s->kt->tbytes});
   for (int l = 0; l < 3; ++l)
     if (s->th[l]) live.push_back({s->th[l], N * s->kt->tbytes});
-  std::vector<void*> snap(live.size(), nullptr);
+}
+
+// Device copies of `live` enqueued on `st` (LBPF_ENOMEM, nothing held, when one does not fit).
+int snapshot_state(const std::vector<std::pair<void*, size_t>>& live, cudaStream_t st, std::vector<void*>& snap) {
+  snap.assign(live.size(), nullptr);
   for (size_t k = 0; k < live.size(); ++k) {
     if (cudaMalloc(&snap[k], live[k].second) != cudaSuccess) {
       cudaGetLastError();
-      for (void* p : snap) if (p) cudaFree(p);
+      for (void*& p : snap) {
+        if (p) cudaFree(p);
+        p = nullptr;
+      }
+      snap.clear();
       return LBPF_ENOMEM;
     }
-    CK(s, cudaMemcpyAsync(snap[k], live[k].first, live[k].second, cudaMemcpyDeviceToDevice, s->stream));
+    if (cudaMemcpyAsync(snap[k], live[k].first, live[k].second, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return LBPF_ECUDA;
+  }
+  return LBPF_OK;
+}
+
+int restore_state(const std::vector<std::pair<void*, size_t>>& live, const std::vector<void*>& snap, cudaStream_t st) {
+  for (size_t k = 0; k < live.size(); ++k)
+    if (cudaMemcpyAsync(live[k].first, snap[k], live[k].second, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return LBPF_ECUDA;
+  return LBPF_OK;
+}
+
+void free_all(std::vector<void*>& snap) {
+  for (void* p : snap)
+    if (p) cudaFree(p);
+  snap.clear();
+}
+}  // namespace
+
+extern "C" {
+
+int lbpf_autotune(lbpf_sim* s, int32_t steps, double* best_ms) {
+  if (!s || steps < 1) return LBPF_EINVAL;
+  if (status(s)) return s->sticky;
+  CK(s, cudaStreamSynchronize(s->stream));
+  std::vector<std::pair<void*, size_t>> live;
+  live_state(s, live);
+  std::vector<void*> snap;
+  const int src = snapshot_state(live, s->stream, snap);
+  if (src != LBPF_OK) {
+    free_all(snap);
+    if (src == LBPF_ECUDA) s->sticky = LBPF_ECUDA;
+    return src;
   }
   const int64_t steps0 = s->steps;
   const int by0 = s->by, zc0 = s->zchunk;
@@ -790,19 +1003,18 @@ int lbpf_autotune(lbpf_sim* s, int32_t steps, double* best_ms) {
         bbest = by;
         zbest = zc;
       }
-      // restore the snapshot and the step counter
-      for (size_t k = 0; k < live.size(); ++k) {
-        void* dst = live[k].first;
-        // populations of the current parity live in pop[par] (the counter is reset below)
-        CK(s, cudaMemcpyAsync(dst, snap[k], live[k].second, cudaMemcpyDeviceToDevice, s->stream));
-      }
+      // back to the snapshot and the step counter (the parity the snapshot was taken at)
       s->steps = steps0;
-      CK(s, cudaStreamSynchronize(s->stream));
+      if (restore_state(live, snap, s->stream) != LBPF_OK || cudaStreamSynchronize(s->stream) != cudaSuccess) {
+        s->sticky = LBPF_ECUDA;
+        free_all(snap);
+        return LBPF_ECUDA;
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  for (void* p : snap) cudaFree(p);
+  free_all(snap);
   int rc = apply_tiling(s, bbest, zbest);
   if (best_ms) *best_ms = best;
   return rc;
@@ -824,7 +1036,7 @@ struct CkptHeader {
 
 int lbpf_save(lbpf_sim* s, const char* path) {
   if (!s || !path) return LBPF_EINVAL;
-  if (s->sticky) return s->sticky;
+  if (status(s)) return s->sticky;
   const size_t N = (size_t)s->nsite;
   const int qs[3] = {s->lat.q_phi, s->lat.q_u, s->lat.q_theta};
   std::vector<double> buf[3];
@@ -854,7 +1066,7 @@ int lbpf_save(lbpf_sim* s, const char* path) {
 
 int lbpf_load(lbpf_sim* s, const char* path) {
   if (!s || !path) return LBPF_EINVAL;
-  if (s->sticky) return s->sticky;
+  if (status(s)) return s->sticky;
   FILE* fp = fopen(path, "rb");
   if (!fp) return LBPF_EINVAL;
   CkptHeader hdr{};
@@ -890,10 +1102,12 @@ int lbpf_load(lbpf_sim* s, const char* path) {
 static int batch_tiling(lbpf_batch* b, int by, int zchunk) {
   const KernelTable& t = *b->sims[0]->kt;
   std::vector<WorkItem> items;
+  std::vector<TileGeom> geo;
   for (size_t i = 0; i < b->sims.size(); ++i) {
     const lbpf_sim* s = b->sims[i];
     const int zc = zchunk > 0 ? std::min(zchunk, s->kg.nz) : default_zchunk(s->kg.nx, s->kg.ny, s->kg.nz, by);
     build_items((int)i, s->kg.nx, s->kg.ny, s->kg.nz, by, zc, items);
+    geo.push_back(TileGeom{s->kg.nx, s->kg.ny, s->kg.nz, zc});
   }
   // interleave large and small simulations: sort items by descending z-chunk work
   std::stable_sort(items.begin(), items.end(),
@@ -907,11 +1121,26 @@ static int batch_tiling(lbpf_batch* b, int by, int zchunk) {
   }
   b->nitems = (int)items.size();
   b->by = by;
+  b->zchunk = zchunk;
+  {
+    const lbpf_lattice& l = b->sims[0]->lat;
+    const int v = block_variant(l.q_phi, by);
+    b->fphi = t.phi[q_index(l.q_phi)][v];
+    b->futh = t.uth[q_index(l.q_u)][qt_index(l.q_theta)][v];
+  }
   b->smem_phi = phi_smem_bytes(t, b->sims[0]->lat.q_phi, by);
   b->smem_uth = uth_smem_bytes(t, b->sims[0]->lat.q_u, b->sims[0]->lat.q_theta, by);
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   b->gexec = nullptr;
   b->graph_ok = false;
+  if (b->ol.on) {
+    const lbpf_lattice& l = b->sims[0]->lat;
+    const int rc = setup_one_launch(b->ol, items, geo, by, step_smem_bytes(t, l.q_phi, l.q_u, l.q_theta, by),
+                                    t.step_fn[q_index(l.q_phi)][q_index(l.q_u)][qt_index(l.q_theta)],
+                                    b->sims[0]->device);
+    if (rc != LBPF_OK) return rc;
+    for (lbpf_sim* s : b->sims) s->batch_err = b->ol.h_err;
+  }
   return LBPF_OK;
 }
 
@@ -921,15 +1150,14 @@ int batch_init(lbpf_batch* b) {
   lbpf_sim* s0 = b->sims[0];
   for (lbpf_sim* s : b->sims) {
     if (!s) return LBPF_EINVAL;
-    if (s->sticky) return s->sticky;
+    if (status(s)) return s->sticky;
     if (memcmp(&s->lat, &s0->lat, sizeof(lbpf_lattice)) != 0 || s->p.storage != s0->p.storage || s->device != s0->device)
       return LBPF_EINVAL;
   }
   const KernelTable& t = *s0->kt;
   const size_t n = b->sims.size();
   for (lbpf_sim* s : b->sims) cudaStreamSynchronize(s->stream);
-  b->fphi = s0->fphi;
-  b->futh = s0->futh;
+  b->ol.fn = s0->ol.fn;
   bool ok = cudaMallocHost(&b->h_desc, n * sizeof(SimDev)) == cudaSuccess;
   ok = ok && cudaMalloc(&b->dd, n * sizeof(SimDev)) == cudaSuccess;
   if (ok) {
@@ -942,8 +1170,10 @@ int batch_init(lbpf_batch* b) {
   ok = ok && cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) == cudaSuccess;
   ok = ok && batch_tiling(b, lattice_is_2d(s0->lat.q_phi) ? 1 : MAX_BLOCK_ROWS, 0) == LBPF_OK;
   const int a = q_index(s0->lat.q_phi), qb = q_index(s0->lat.q_u), qc = qt_index(s0->lat.q_theta);
-  ok = ok && raise_smem_limit(t.phi_fn[a], s0->device) == LBPF_OK;
-  ok = ok && raise_smem_limit(t.uth_fn[qb][qc], s0->device) == LBPF_OK;
+  for (int v = 0; v < 2; ++v) {
+    ok = ok && raise_smem_limit(t.phi_fn[a][v], s0->device) == LBPF_OK;
+    ok = ok && raise_smem_limit(t.uth_fn[qb][qc][v], s0->device) == LBPF_OK;
+  }
   if (!ok) {
     cudaGetLastError();
     return LBPF_ENOMEM;
@@ -1030,7 +1260,7 @@ int lbpf_batch_step(lbpf_batch* b, int64_t n) {
   if (!b || n < 0) return LBPF_EINVAL;
   const int64_t st0 = b->sims[0]->steps;
   for (lbpf_sim* s : b->sims) {
-    if (s->sticky) return s->sticky;
+    if (status(s)) return s->sticky;
     if (s->steps != st0) return LBPF_EINVAL;  // batch members advance in lockstep
   }
   // work the members enqueued on their own streams comes first
@@ -1047,7 +1277,7 @@ int lbpf_batch_step(lbpf_batch* b, int64_t n) {
     if (s6 == 0 && n >= kGraphSteps) {
       if (!b->graph_ok) {
         if (capture_graph(b->stream, b->fphi, b->futh, b->nitems, b->by, b->smem_phi, b->smem_uth, b->dd, b->d_items,
-                          &b->gexec) != LBPF_OK)
+                          &b->ol, &b->gexec) != LBPF_OK)
           return LBPF_ECUDA;
         b->graph_ok = true;
       }
@@ -1055,7 +1285,8 @@ int lbpf_batch_step(lbpf_batch* b, int64_t n) {
       steps += kGraphSteps;
       n -= kGraphSteps;
     } else {
-      if (launch_step(b->stream, b->fphi, b->futh, b->nitems, b->by, b->smem_phi, b->smem_uth, b->dd, b->d_items, s6) !=
+      if (launch_step(b->stream, b->fphi, b->futh, b->nitems, b->by, b->smem_phi, b->smem_uth, b->dd, b->d_items, s6,
+                      &b->ol) !=
           LBPF_OK)
         return LBPF_ECUDA;
       steps += 1;
@@ -1073,10 +1304,105 @@ int lbpf_batch_step(lbpf_batch* b, int64_t n) {
 int lbpf_batch_set_tiling(lbpf_batch* b, int32_t by, int32_t zchunk) {
   if (!b || by < 0 || zchunk < 0 || (by && (by < 4 || by > MAX_BLOCK_ROWS))) return LBPF_EINVAL;
   for (lbpf_sim* s : b->sims)
-    if (s->sticky) return s->sticky;
+    if (status(s)) return s->sticky;
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return LBPF_ECUDA;
   if (lattice_is_2d(b->sims[0]->lat.q_phi)) by = 1;  // 2D: one-row blocks
   return batch_tiling(b, by ? by : b->by, zchunk);
+}
+
+int lbpf_batch_set_schedule(lbpf_batch* b, int32_t schedule) {
+  if (!b || (schedule != LBPF_SCHED_TWO_KERNELS && schedule != LBPF_SCHED_ONE_LAUNCH)) return LBPF_EINVAL;
+  for (lbpf_sim* s : b->sims)
+    if (status(s)) return s->sticky;
+  if (schedule == LBPF_SCHED_ONE_LAUNCH && !b->ol.fn) return LBPF_EINVAL;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return LBPF_ECUDA;
+  const bool was = b->ol.on;
+  b->ol.on = schedule == LBPF_SCHED_ONE_LAUNCH;
+  const int rc = batch_tiling(b, b->by, b->zchunk);
+  if (rc != LBPF_OK) {
+    b->ol.on = was;
+    free_one_launch(b->ol);
+    batch_tiling(b, b->by, b->zchunk);
+  }
+  if (!b->ol.on) free_one_launch(b->ol);
+  return rc;
+}
+
+int lbpf_batch_get_schedule(const lbpf_batch* b, int32_t* schedule) {
+  if (!b || !schedule) return LBPF_EINVAL;
+  *schedule = b->ol.on ? LBPF_SCHED_ONE_LAUNCH : LBPF_SCHED_TWO_KERNELS;
+  return LBPF_OK;
+}
+
+int lbpf_batch_get_tiling(const lbpf_batch* b, int32_t* by, int32_t* zchunk) {
+  if (!b) return LBPF_EINVAL;
+  if (by) *by = b->by;
+  if (zchunk) *zchunk = b->zchunk;
+  return LBPF_OK;
+}
+
+int lbpf_batch_autotune(lbpf_batch* b, int32_t steps, double* best_ms) {
+  if (!b || steps < 1) return LBPF_EINVAL;
+  const int64_t st0 = b->sims[0]->steps;
+  for (lbpf_sim* s : b->sims) {
+    if (status(s)) return s->sticky;
+    if (s->steps != st0) return LBPF_EINVAL;
+  }
+  for (lbpf_sim* s : b->sims)
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return LBPF_ECUDA;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return LBPF_ECUDA;
+  std::vector<std::pair<void*, size_t>> live;
+  for (lbpf_sim* s : b->sims) live_state(s, live);
+  std::vector<void*> snap;
+  int rc = snapshot_state(live, b->stream, snap);
+  if (rc != LBPF_OK) {
+    free_all(snap);
+    return rc;
+  }
+  // every trial times whole graph periods: single steps up to a period boundary, one period of
+  // warm-up (it also captures the trial's graph), then `steps` rounded up to whole periods
+  const int64_t align = (kGraphSteps - st0 % kGraphSteps) % kGraphSteps;
+  const int64_t timed = ((int64_t)steps + kGraphSteps - 1) / kGraphSteps * kGraphSteps;
+  const bool is2d = lattice_is_2d(b->sims[0]->lat.q_phi);
+  std::vector<std::pair<int, int>> cand;
+  if (is2d) {
+    for (int zc : {0, 8, 16, 32}) cand.push_back({1, zc});
+  } else {
+    for (int by : {4, 6, 8})
+      for (int zc : {0, 12, 16, 24}) cand.push_back({by, zc});
+  }
+  const int by0 = b->by, zc0 = b->zchunk;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  bool ok = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+  double best = 1e300;
+  int bbest = by0, zbest = zc0;
+  for (size_t c = 0; c < cand.size() && ok; ++c) {
+    if (batch_tiling(b, cand[c].first, cand[c].second) != LBPF_OK) continue;
+    rc = lbpf_batch_step(b, align + kGraphSteps);
+    ok = cudaEventRecord(e0, b->stream) == cudaSuccess;
+    if (rc == LBPF_OK && ok) rc = lbpf_batch_step(b, timed);
+    ok = ok && cudaEventRecord(e1, b->stream) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+    float ms = 0;
+    ok = ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+    if (ok && rc == LBPF_OK && ms / timed < best) {
+      best = ms / timed;
+      bbest = cand[c].first;
+      zbest = cand[c].second;
+    }
+    // every member back to the snapshot and its step count
+    for (lbpf_sim* s : b->sims) s->steps = st0;
+    ok = ok && restore_state(live, snap, b->stream) == LBPF_OK && cudaStreamSynchronize(b->stream) == cudaSuccess;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  free_all(snap);
+  if (!ok) {
+    for (lbpf_sim* s : b->sims) s->sticky = LBPF_ECUDA;
+    return LBPF_ECUDA;
+  }
+  rc = batch_tiling(b, bbest, zbest);
+  if (best_ms) *best_ms = best;
+  return rc;
 }
 
 int lbpf_batch_destroy(lbpf_batch* b) {
@@ -1087,6 +1413,14 @@ int lbpf_batch_destroy(lbpf_batch* b) {
   if (b->h_desc) cudaFreeHost(b->h_desc);
   if (b->d_items) cudaFree(b->d_items);
   if (b->ev) cudaEventDestroy(b->ev);
+  // borrowed members outlive the batch: they keep a failure the batch saw, not its flag
+  for (lbpf_sim* s : b->sims)
+    if (s && b->ol.h_err && s->batch_err == b->ol.h_err) {
+      status(s);
+      s->batch_err = nullptr;
+    }
+  free_one_launch(b->ol);
+  if (b->ol.h_err) cudaFreeHost(b->ol.h_err);
   if (b->owns_sims)
     for (lbpf_sim* s : b->sims) lbpf_destroy(s);
   if (b->own_stream) cudaStreamDestroy(b->stream);

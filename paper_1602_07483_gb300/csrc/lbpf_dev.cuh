@@ -34,6 +34,8 @@
 
 #include <type_traits>
 
+#include "lbpf_plan.h"
+
 namespace lbpf {
 
 // ---------------------------------------------------------------- lattices
@@ -326,13 +328,6 @@ struct SimDev {
   double scale[3], inv_scale[3]; // FP16/BF16 codec scales of g, h, f
 };
 
-struct WorkItem {
-  int sim;
-  int x0, y0;  // first interior column of the tile
-  int z0, z1;  // planes [z0, z1) written by this block
-};
-
-constexpr int TILE_X = 30;  // interior columns per block row (block x = 32)
 #ifndef LBPF_MAX_BLOCK_ROWS
 #define LBPF_MAX_BLOCK_ROWS 8
 #endif
@@ -446,11 +441,14 @@ struct RingMap {
 template <typename T>
 struct RingRegs {
   T v[RPT];
+  // CG: through L2 (ld.global.cg) instead of the read-only path, for data written earlier
+  // in the same launch
+  template <bool CG = false>
   __device__ __forceinline__ void fetch(const RingMap& m, const T* __restrict__ src, int z, int nz, long long plane) {
     const T* p = src + (long long)min(max(z, 0), nz - 1) * plane;
 #pragma unroll
     for (int r = 0; r < RPT; ++r)
-      if (m.off[r] >= 0) v[r] = ldro(p + m.off[r]);
+      if (m.off[r] >= 0) v[r] = CG ? __ldcg(p + m.off[r]) : ldro(p + m.off[r]);
   }
   __device__ __forceinline__ void store(const RingMap& m, T* __restrict__ dst, int tid, int nthr) const {
 #pragma unroll
@@ -460,19 +458,19 @@ struct RingRegs {
 };
 
 // ---------------------------------------------------------------- phase field
-template <int QP, typename S>
-__global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_PHI64_MIN_BLOCKS
-                                                       : (Lat<QP>::has_y ? LBPF_PHI_MIN_BLOCKS : LBPF_PHI2D_MIN_BLOCKS)) k_phi(const SimDev* __restrict__ sims, const WorkItem* __restrict__ items,
-                                                int s6) {
+// One tile of the phase-field phase: the block's 30 x (BY-2) columns over planes [z0, z1).
+// BYC: the block height BY when fixed at compile time (its index arithmetic then folds into
+// constants), 0 to take it from blockDim.y.
+template <int QP, typename S, int BYC>
+__device__ __forceinline__ void phi_tile(const SimDev* __restrict__ sims, const WorkItem it, int s6) {
   using C = Codec<S>;
   using T = typename C::T;
   using L = Lat<QP>;
   using YS = YSlots<QP>;
   constexpr int NY = NYOf<QP>::value;
-  const WorkItem it = items[blockIdx.x];
   const SimDev& sd = sims[it.sim];
   const int nx = sd.nx, ny = sd.ny, nz = sd.nz;
-  const int BY = blockDim.y;
+  const int BY = BYC > 0 ? BYC : (int)blockDim.y;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * 32 + tx, nthr = 32 * BY;
   const int x = it.x0 - 1 + tx;
@@ -745,11 +743,18 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_PHI
   }
 }
 
-// ---------------------------------------------------------------- U and theta
-template <int QU, int QT, typename S>
-__global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_UTH64_MIN_BLOCKS
-                                                       : (Lat<QU>::has_y ? LBPF_UTH_MIN_BLOCKS : LBPF_UTH2D_MIN_BLOCKS)) k_uth(const SimDev* __restrict__ sims, const WorkItem* __restrict__ items,
+template <int QP, typename S, int BYC>
+__global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_PHI64_MIN_BLOCKS
+                                                       : (Lat<QP>::has_y ? LBPF_PHI_MIN_BLOCKS : LBPF_PHI2D_MIN_BLOCKS)) k_phi(const SimDev* __restrict__ sims, const WorkItem* __restrict__ items,
                                                 int s6) {
+  phi_tile<QP, S, BYC>(sims, items[blockIdx.x], s6);
+}
+
+// ---------------------------------------------------------------- U and theta
+// One tile of the U/theta phase.  COH: phi^{n+1} is read through L2 (ld.global.cg), for
+// launches in which other blocks of the same launch write it.  BYC as for phi_tile.
+template <int QU, int QT, typename S, bool COH, int BYC>
+__device__ __forceinline__ void uth_tile(const SimDev* __restrict__ sims, const WorkItem it, int s6) {
   using C = Codec<S>;
   using T = typename C::T;
   using LU = Lat<QU>;
@@ -759,10 +764,9 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_UTH
   constexpr int NYU = NYOf<QU>::value;
   constexpr int NYT = NYOf<QT>::value;
   constexpr int QTA = QT > 0 ? QT : 1;
-  const WorkItem it = items[blockIdx.x];
   const SimDev& sd = sims[it.sim];
   const int nx = sd.nx, ny = sd.ny, nz = sd.nz;
-  const int BY = blockDim.y;
+  const int BY = BYC > 0 ? BYC : (int)blockDim.y;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * 32 + tx, nthr = 32 * BY;
   const int x = it.x0 - 1 + tx;
@@ -805,7 +809,7 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_UTH
   {
     RingRegs<T> a;
     for (int z = zlo - 1; z <= zlo + 1; ++z) {
-      a.fetch(rm, phi1, z, nz, plane);
+      a.template fetch<COH>(rm, phi1, z, nz, plane);
       a.store(rm, ring + slot4(z) * RS, tid, nthr);
       if (TSH) {
         a.fetch(rm, thm, z, nz, plane);
@@ -815,7 +819,7 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_UTH
   }
   RingRegs<T> pf, pft;
   if (zlo + 2 <= zhi + 1) {
-    pf.fetch(rm, phi1, zlo + 2, nz, plane);
+    pf.template fetch<COH>(rm, phi1, zlo + 2, nz, plane);
     if (TSH) pft.fetch(rm, thm, zlo + 2, nz, plane);
   }
   T u0A = 0, u1A = 0, u2A = 0, t0A = 0, t1A = 0, t2A = 0;
@@ -1080,7 +1084,7 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_UTH
       if (TSH) pft.store(rm, ringt + slot4(zc + 2) * RS, tid, nthr);
     }
     if (zc + 3 <= zhi + 1) {
-      pf.fetch(rm, phi1, zc + 3, nz, plane);
+      pf.template fetch<COH>(rm, phi1, zc + 3, nz, plane);
       if (TSH) pft.fetch(rm, thm, zc + 3, nz, plane);
     }
     __syncthreads();
@@ -1165,6 +1169,92 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_UTH
     };
     gather_row(0, u0A, u1A, u2A, t0A, t1A, t2A);
     buf ^= 1;
+  }
+}
+
+template <int QU, int QT, typename S, int BYC>
+__global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_UTH64_MIN_BLOCKS
+                                                       : (Lat<QU>::has_y ? LBPF_UTH_MIN_BLOCKS : LBPF_UTH2D_MIN_BLOCKS)) k_uth(const SimDev* __restrict__ sims, const WorkItem* __restrict__ items,
+                                                int s6) {
+  uth_tile<QU, QT, S, false, BYC>(sims, items[blockIdx.x], s6);
+}
+
+// ---------------------------------------------------------------- one launch per step
+// Both phases of a step in one persistent launch, so that tiles of the phase-field phase
+// (bound by instruction issue) run beside tiles of the U/theta phase (bound by memory
+// latency) on the same SMs.  Blocks draw tickets in order from a counter; ticket t names
+// the phase-field tile or the U/theta tile of one work item.  The U/theta tile of an item
+// reads phi^{n+1} over its ring (two nodes around its columns and rows, two planes around
+// its z-chunk), so it waits for the done flags of the phase-field tiles that write that
+// region; the host orders the tickets so that those tiles always come earlier, and a
+// block draws a ticket only while it runs, so no wait depends on a tile that has not
+// started.  The U/theta tiles read nothing else that the launch writes (the phase-field
+// tiles write g at the other buffer parity and the new phi level; the U/theta tiles write
+// h, f, U and theta at levels the phase-field tiles do not read).  The waits are bounded
+// all the same: after about a second a wait gives up, sets *err (host-visible) and the tile
+// goes ahead; the host then reports the step as failed.
+struct StepSched {
+  const int* order;    // ticket -> j >= 0: phase-field tile of item j; ~j: U/theta tile of item j
+  const int* dep_off;  // the U/theta tile of item j waits for the phase-field tiles dep[dep_off[j] .. dep_off[j+1])
+  const int* dep;
+  unsigned* ctl;       // ctl[0]: next ticket; ctl[1 + j]: phase-field tile of item j done (zeroed before each launch)
+  int* err;            // set to 1 when a wait gave up
+  int ntickets;
+};
+
+#ifndef LBPF_WAIT_POLLS
+#define LBPF_WAIT_POLLS (1u << 22)  // polls of about 0.25 us each: about a second
+#endif
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// One full warp waits until done[dep[k]] != 0 for every k < n, each lane polling a share
+// of the flags; false when `polls` rounds passed without that.
+__device__ __forceinline__ bool wait_done(const unsigned* done, const int* dep, int n, unsigned polls) {
+  const int lane = threadIdx.x & 31;
+  for (unsigned r = 0; r < polls; ++r) {
+    bool ok = true;
+    for (int k = lane; k < n; k += 32) ok = ok && ld_acquire_gpu(done + __ldg(dep + k)) != 0u;
+    if (__all_sync(0xffffffffu, ok)) return true;
+    __nanosleep(200);
+  }
+  return false;
+}
+
+template <int QP, int QU, int QT, typename S>
+__global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_UTH64_MIN_BLOCKS
+                                                       : (Lat<QU>::has_y ? LBPF_UTH_MIN_BLOCKS : LBPF_UTH2D_MIN_BLOCKS)) k_step(const SimDev* __restrict__ sims, const WorkItem* __restrict__ items,
+                                                const StepSched sc, int s6) {
+  __shared__ int s_ticket;
+  const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+  for (;;) {
+    if (lead) s_ticket = (int)atomicAdd(sc.ctl, 1u);
+    __syncthreads();
+    const int t = s_ticket;
+    if (t >= sc.ntickets) return;  // the same for every thread of the block
+    const int w = __ldg(sc.order + t);
+    if (w >= 0) {
+      phi_tile<QP, S, 0>(sims, items[w], s6);
+      __threadfence();  // this thread's phi^{n+1} stores are visible before the flag
+      __syncthreads();
+      if (lead) st_release_gpu(sc.ctl + 1 + w, 1u);
+    } else {
+      const int j = ~w;
+      if (threadIdx.y == 0) {
+        const int b = __ldg(sc.dep_off + j), n = __ldg(sc.dep_off + j + 1) - b;
+        if (!wait_done(sc.ctl + 1, sc.dep + b, n, LBPF_WAIT_POLLS) && threadIdx.x == 0) atomicExch(sc.err, 1);
+      }
+      __syncthreads();
+      uth_tile<QU, QT, S, true, 0>(sims, items[j], s6);
+      __syncthreads();  // the next tile reuses the shared memory
+    }
   }
 }
 

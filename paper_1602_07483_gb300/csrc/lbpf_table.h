@@ -11,17 +11,26 @@ struct LatRT;
 
 using StepLaunch = cudaError_t (*)(dim3 grid, dim3 block, size_t smem, cudaStream_t st, const SimDev* sims,
                                    const WorkItem* items, int s6);
+using OneLaunchFn = cudaError_t (*)(dim3 grid, dim3 block, size_t smem, cudaStream_t st, const SimDev* sims,
+                                    const WorkItem* items, const StepSched& sc, int s6);
 
 struct KernelTable {
   int sbytes;            // bytes per stored population
   int tbytes;            // bytes of the compute type
   bool shifted;          // FP16/BF16 codec
   // indexed by lattice_slot(q): 7, 15, 19, 5, 9; theta additionally 0 (frozen) in the last slot.
-  // Only pairings of one dimension are instantiated (the others are null).
-  StepLaunch phi[5];
-  StepLaunch uth[5][6];
-  const void* phi_fn[5];
-  const void* uth_fn[5][6];
+  // Only pairings of one dimension are instantiated (the others are null).  Last index: the
+  // block-height variant (block_variant): 1 for blocks of the height compiled in (8 rows in
+  // 3D, one row in 2D), 0 for any height (the 2D entries are the one-row kernel in both).
+  StepLaunch phi[5][2];
+  StepLaunch uth[5][6][2];
+  const void* phi_fn[5][2];
+  const void* uth_fn[5][6][2];
+  // one-launch step kernels (k_step) by phi, U and theta slots; null where not instantiated
+  // (FP64, and lattice triples other than D3Q19 x D3Q19 x {frozen, D3Q7, D3Q19} and
+  // D2Q9 x D2Q5 x D2Q5)
+  OneLaunchFn step[5][5][6];
+  const void* step_fn[5][5][6];
   cudaError_t (*init_scalar)(cudaStream_t, int nx, int ny, int nz, const double* cen, const double* rad, int nseed,
                              double c, void* out);
   cudaError_t (*init_pop)(cudaStream_t, const SimDev& sd, const LatRT& Lp, const LatRT& Lu, const LatRT& Lt,
@@ -39,6 +48,16 @@ struct KernelTable {
   cudaError_t (*tip)(cudaStream_t, const void* phi, int nx, int ny, int nz, int axis, int cx, int cy, int cz,
                      double* out);
 };
+
+// kernels compiled in translation units of their own (parallel compilation): the
+// 8-row 3D step kernels of each storage type, and the one-launch step kernels
+void add_fixed_kernels_f64(KernelTable& t);
+void add_fixed_kernels_f32(KernelTable& t);
+void add_fixed_kernels_f16(KernelTable& t);
+void add_fixed_kernels_bf16(KernelTable& t);
+void add_step_kernels_f32(KernelTable& t);
+void add_step_kernels_f16(KernelTable& t);
+void add_step_kernels_bf16(KernelTable& t);
 
 const KernelTable& table_f64();
 const KernelTable& table_f32();
@@ -59,6 +78,10 @@ inline int lattice_slot(int q) {
 }
 inline bool lattice_is_2d(int q) { return q == 5 || q == 9; }
 
+// kernel variant for blocks of `by` rows: the compiled-in height (MAX_BLOCK_ROWS in 3D, one
+// row in 2D) or the general kernel
+inline int block_variant(int q_phi, int by) { return by == (lattice_is_2d(q_phi) ? 1 : MAX_BLOCK_ROWS) ? 1 : 0; }
+
 // populations with e_y != 0 (they cross block rows in the moment gather)
 inline int ny_count(int q) {
   switch (q) {
@@ -78,6 +101,10 @@ inline size_t phi_smem_bytes(const KernelTable& t, int qp, int by) {
 inline size_t uth_smem_bytes(const KernelTable& t, int qu, int qt, int by) {
   const size_t rs = 34u * (size_t)(by + 2);
   return ((t.shifted && qt ? 8 : 4) * rs + 2 * (size_t)(ny_count(qu) + ny_count(qt)) * 32u * by) * t.tbytes;
+}
+inline size_t step_smem_bytes(const KernelTable& t, int qp, int qu, int qt, int by) {
+  const size_t a = phi_smem_bytes(t, qp, by), b = uth_smem_bytes(t, qu, qt, by);
+  return a > b ? a : b;
 }
 
 }  // namespace lbpf

@@ -16,18 +16,36 @@ inline int aux_blocks(long long n) {
   return (int)(b < 1 ? 1 : b);
 }
 
-template <int QP, typename S>
+template <int QP, typename S, int BYC>
 cudaError_t launch_phi(dim3 g, dim3 b, size_t smem, cudaStream_t st, const SimDev* sims, const WorkItem* items,
                        int s6) {
-  k_phi<QP, S><<<g, b, smem, st>>>(sims, items, s6);
+  k_phi<QP, S, BYC><<<g, b, smem, st>>>(sims, items, s6);
   return cudaGetLastError();
 }
 
-template <int QU, int QT, typename S>
+template <int QU, int QT, typename S, int BYC>
 cudaError_t launch_uth(dim3 g, dim3 b, size_t smem, cudaStream_t st, const SimDev* sims, const WorkItem* items,
                        int s6) {
-  k_uth<QU, QT, S><<<g, b, smem, st>>>(sims, items, s6);
+  k_uth<QU, QT, S, BYC><<<g, b, smem, st>>>(sims, items, s6);
   return cudaGetLastError();
+}
+
+template <int QP, int QU, int QT, typename S>
+cudaError_t launch_step_one(dim3 g, dim3 b, size_t smem, cudaStream_t st, const SimDev* sims, const WorkItem* items,
+                            const StepSched& sc, int s6) {
+  k_step<QP, QU, QT, S><<<g, b, smem, st>>>(sims, items, sc, s6);
+  return cudaGetLastError();
+}
+
+// The lattice triples with a one-launch step kernel: the paper's 3D benchmarks (D3Q19 for
+// phi and U with theta frozen, on D3Q7 or on D3Q19) and its 2D set (D2Q9, D2Q5, D2Q5).
+template <typename S>
+void fill_step_kernels(KernelTable& t) {
+#define LBPF_STEP(qa, qb, qc)                                                                     \
+  t.step[lattice_slot(qa)][lattice_slot(qb)][lattice_slot(qc)] = launch_step_one<qa, qb, qc, S>; \
+  t.step_fn[lattice_slot(qa)][lattice_slot(qb)][lattice_slot(qc)] = (const void*)k_step<qa, qb, qc, S>;
+  LBPF_STEP(19, 19, 0) LBPF_STEP(19, 19, 7) LBPF_STEP(19, 19, 19) LBPF_STEP(9, 5, 5)
+#undef LBPF_STEP
 }
 
 template <typename S>
@@ -77,26 +95,59 @@ struct AuxImpl {
   }
 };
 
+// The two-kernel step's kernels for blocks of any height (3D) and the one-row kernels (2D).
+template <typename S>
+void fill_step_kernels_general(KernelTable& t) {
+#define LBPF_PHI3(q)                                          \
+  t.phi[lattice_slot(q)][0] = launch_phi<q, S, 0>;             \
+  t.phi_fn[lattice_slot(q)][0] = (const void*)k_phi<q, S, 0>;
+#define LBPF_PHI2(q)                                                                       \
+  t.phi[lattice_slot(q)][0] = t.phi[lattice_slot(q)][1] = launch_phi<q, S, 1>;              \
+  t.phi_fn[lattice_slot(q)][0] = t.phi_fn[lattice_slot(q)][1] = (const void*)k_phi<q, S, 1>;
+  LBPF_PHI3(7) LBPF_PHI3(15) LBPF_PHI3(19) LBPF_PHI2(5) LBPF_PHI2(9)
+#undef LBPF_PHI3
+#undef LBPF_PHI2
+#define LBPF_UTH3(qa, qb)                                                            \
+  t.uth[lattice_slot(qa)][lattice_slot(qb)][0] = launch_uth<qa, qb, S, 0>;            \
+  t.uth_fn[lattice_slot(qa)][lattice_slot(qb)][0] = (const void*)k_uth<qa, qb, S, 0>;
+#define LBPF_UTH2(qa, qb)                                                                              \
+  t.uth[lattice_slot(qa)][lattice_slot(qb)][0] = t.uth[lattice_slot(qa)][lattice_slot(qb)][1] =         \
+      launch_uth<qa, qb, S, 1>;                                                                        \
+  t.uth_fn[lattice_slot(qa)][lattice_slot(qb)][0] = t.uth_fn[lattice_slot(qa)][lattice_slot(qb)][1] =   \
+      (const void*)k_uth<qa, qb, S, 1>;
+  LBPF_UTH3(7, 0) LBPF_UTH3(7, 7) LBPF_UTH3(7, 15) LBPF_UTH3(7, 19)
+  LBPF_UTH3(15, 0) LBPF_UTH3(15, 7) LBPF_UTH3(15, 15) LBPF_UTH3(15, 19)
+  LBPF_UTH3(19, 0) LBPF_UTH3(19, 7) LBPF_UTH3(19, 15) LBPF_UTH3(19, 19)
+  LBPF_UTH2(5, 0) LBPF_UTH2(5, 5) LBPF_UTH2(5, 9)
+  LBPF_UTH2(9, 0) LBPF_UTH2(9, 5) LBPF_UTH2(9, 9)
+#undef LBPF_UTH3
+#undef LBPF_UTH2
+}
+
+// The 3D two-kernel step's kernels compiled for blocks of MAX_BLOCK_ROWS rows.
+template <typename S>
+void fill_step_kernels_fixed(KernelTable& t) {
+#define LBPF_PHI3(q)                                                         \
+  t.phi[lattice_slot(q)][1] = launch_phi<q, S, MAX_BLOCK_ROWS>;               \
+  t.phi_fn[lattice_slot(q)][1] = (const void*)k_phi<q, S, MAX_BLOCK_ROWS>;
+  LBPF_PHI3(7) LBPF_PHI3(15) LBPF_PHI3(19)
+#undef LBPF_PHI3
+#define LBPF_UTH3(qa, qb)                                                                           \
+  t.uth[lattice_slot(qa)][lattice_slot(qb)][1] = launch_uth<qa, qb, S, MAX_BLOCK_ROWS>;              \
+  t.uth_fn[lattice_slot(qa)][lattice_slot(qb)][1] = (const void*)k_uth<qa, qb, S, MAX_BLOCK_ROWS>;
+  LBPF_UTH3(7, 0) LBPF_UTH3(7, 7) LBPF_UTH3(7, 15) LBPF_UTH3(7, 19)
+  LBPF_UTH3(15, 0) LBPF_UTH3(15, 7) LBPF_UTH3(15, 15) LBPF_UTH3(15, 19)
+  LBPF_UTH3(19, 0) LBPF_UTH3(19, 7) LBPF_UTH3(19, 15) LBPF_UTH3(19, 19)
+#undef LBPF_UTH3
+}
+
 template <typename S>
 KernelTable build_table() {
   KernelTable t{};
   t.sbytes = (int)sizeof(S);
   t.tbytes = (int)sizeof(typename Codec<S>::T);
   t.shifted = Codec<S>::shifted;
-#define LBPF_PHI(q)                                   \
-  t.phi[lattice_slot(q)] = launch_phi<q, S>;          \
-  t.phi_fn[lattice_slot(q)] = (const void*)k_phi<q, S>;
-  LBPF_PHI(7) LBPF_PHI(15) LBPF_PHI(19) LBPF_PHI(5) LBPF_PHI(9)
-#undef LBPF_PHI
-#define LBPF_UTH(qa, qb)                                                \
-  t.uth[lattice_slot(qa)][lattice_slot(qb)] = launch_uth<qa, qb, S>;    \
-  t.uth_fn[lattice_slot(qa)][lattice_slot(qb)] = (const void*)k_uth<qa, qb, S>;
-  LBPF_UTH(7, 0) LBPF_UTH(7, 7) LBPF_UTH(7, 15) LBPF_UTH(7, 19)
-  LBPF_UTH(15, 0) LBPF_UTH(15, 7) LBPF_UTH(15, 15) LBPF_UTH(15, 19)
-  LBPF_UTH(19, 0) LBPF_UTH(19, 7) LBPF_UTH(19, 15) LBPF_UTH(19, 19)
-  LBPF_UTH(5, 0) LBPF_UTH(5, 5) LBPF_UTH(5, 9)
-  LBPF_UTH(9, 0) LBPF_UTH(9, 5) LBPF_UTH(9, 9)
-#undef LBPF_UTH
+  fill_step_kernels_general<S>(t);
   t.init_scalar = AuxImpl<S>::init_scalar;
   t.init_pop = AuxImpl<S>::init_pop;
   t.pack = AuxImpl<S>::pack;

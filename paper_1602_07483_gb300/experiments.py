@@ -201,38 +201,15 @@ def anisotropy(n=301, storage="f32", steps=None):
     return out
 
 
-def _tune_batch_tiling(sims, steps=24):
-    """Fastest batch tiling (block rows, z-chunk) for these simulations, timed on
-    throwaway copies so that the measured run starts from the seeds."""
-    members = [lbpf.sim_from_workload(w) for w in sims]
-    batch = lbpf.Batch(members)
-    best, best_t = (0, 0), None
-    for by in (4, 6, 8):
-        for zc in (0, 16):
-            batch.set_tiling(by, zc)
-            batch.step(6)
-            _sync()
-            t0 = time.perf_counter()
-            batch.step(steps)
-            _sync()
-            el = time.perf_counter() - t0
-            if best_t is None or el < best_t:
-                best, best_t = (by, zc), el
-    batch.close()
-    for m in members:
-        m.close()
-    return best
-
-
 def sweep(count=64, steps=2000, baseline_steps=200):
     """The batched sweep: `count` uneven FP16-storage simulations advanced together
-    (tiling tuned first on copies), against the same simulations one by one in FP64."""
+    (tiling autotuned first), against the same simulations one by one in FP64."""
     sims = workloads.batch_sweep(count=count, storage="f16")
     sites = sum(w.sites for w in sims)
-    tiling = _tune_batch_tiling(sims)
     members = [lbpf.sim_from_workload(w) for w in sims]
     batch = lbpf.Batch(members)
-    batch.set_tiling(*tiling)
+    batch.autotune(steps=24)  # fastest tiling kept, members restored to their seeds
+    tiling = batch.get_tiling()
     batch.step(6)
     _sync()
     members[0].sums(check=False)

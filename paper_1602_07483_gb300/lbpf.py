@@ -18,8 +18,9 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "liblbpf.so")
 
-LBPF_OK, LBPF_EINVAL, LBPF_EUNSTABLE, LBPF_ENOMEM, LBPF_ENAN, LBPF_ECUDA = 0, -1, -2, -3, -4, -6
+LBPF_OK, LBPF_EINVAL, LBPF_EUNSTABLE, LBPF_ENOMEM, LBPF_ENAN, LBPF_ETIMEOUT, LBPF_ECUDA = 0, -1, -2, -3, -4, -5, -6
 STORAGE = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+SCHEDULES = {"two_kernels": 0, "one_launch": 1}
 LBPF_PHI, LBPF_U, LBPF_THETA = 1, 2, 4
 
 _LIB = None
@@ -84,6 +85,9 @@ def load(path: str = LIB_PATH):
             "lbpf_set_tiling": ([_VP, i32, i32], ctypes.c_int),
             "lbpf_get_tiling": ([_VP, ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
             "lbpf_autotune": ([_VP, i32, _D], ctypes.c_int),
+            "lbpf_set_schedule": ([_VP, i32], ctypes.c_int),
+            "lbpf_get_schedule": ([_VP, ctypes.POINTER(i32)], ctypes.c_int),
+            "lbpf_wait_probe": ([i32, i32, ctypes.POINTER(i32)], ctypes.c_int),
             "lbpf_destroy": ([_VP], ctypes.c_int),
             "lbpf_batch_create": ([i32, ctypes.POINTER(Grid), ctypes.POINTER(Lattice), ctypes.POINTER(Params), _VP,
                                    ctypes.POINTER(_VP)], ctypes.c_int),
@@ -91,6 +95,10 @@ def load(path: str = LIB_PATH):
             "lbpf_batch_from_sims": ([i32, ctypes.POINTER(_VP), _VP, ctypes.POINTER(_VP)], ctypes.c_int),
             "lbpf_batch_step": ([_VP, i64], ctypes.c_int),
             "lbpf_batch_set_tiling": ([_VP, i32, i32], ctypes.c_int),
+            "lbpf_batch_get_tiling": ([_VP, ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
+            "lbpf_batch_autotune": ([_VP, i32, _D], ctypes.c_int),
+            "lbpf_batch_set_schedule": ([_VP, i32], ctypes.c_int),
+            "lbpf_batch_get_schedule": ([_VP, ctypes.POINTER(i32)], ctypes.c_int),
             "lbpf_batch_destroy": ([_VP], ctypes.c_int),
             "lbpf_strerror": ([ctypes.c_int], ctypes.c_char_p),
         }
@@ -228,6 +236,16 @@ class Sim:
         _check(self._L.lbpf_autotune(self._h, steps, ctypes.byref(ms)), "lbpf_autotune")
         return ms.value
 
+    def set_schedule(self, schedule):
+        """``"two_kernels"`` or ``"one_launch"`` (``lbpf_set_schedule``)."""
+        _check(self._L.lbpf_set_schedule(self._h, SCHEDULES[schedule]), "lbpf_set_schedule")
+
+    @property
+    def schedule(self):
+        v = ctypes.c_int32()
+        _check(self._L.lbpf_get_schedule(self._h, ctypes.byref(v)), "lbpf_get_schedule")
+        return {c: n for n, c in SCHEDULES.items()}[v.value]
+
 
 class Batch:
     """Several simulations advanced together (see ``lbpf_batch_create``).
@@ -273,6 +291,27 @@ class Batch:
     def set_tiling(self, by=0, zchunk=0):
         _check(self._L.lbpf_batch_set_tiling(self._h, int(by), int(zchunk)), "lbpf_batch_set_tiling")
 
+    def get_tiling(self):
+        by, zc = ctypes.c_int32(), ctypes.c_int32()
+        _check(self._L.lbpf_batch_get_tiling(self._h, ctypes.byref(by), ctypes.byref(zc)), "lbpf_batch_get_tiling")
+        return by.value, zc.value
+
+    def autotune(self, steps=12):
+        """Fastest tiling kept, state unchanged (``lbpf_batch_autotune``); ms per step."""
+        ms = ctypes.c_double()
+        _check(self._L.lbpf_batch_autotune(self._h, int(steps), ctypes.byref(ms)), "lbpf_batch_autotune")
+        return ms.value
+
+    def set_schedule(self, schedule):
+        """``"two_kernels"`` or ``"one_launch"`` (``lbpf_batch_set_schedule``)."""
+        _check(self._L.lbpf_batch_set_schedule(self._h, SCHEDULES[schedule]), "lbpf_batch_set_schedule")
+
+    @property
+    def schedule(self):
+        v = ctypes.c_int32()
+        _check(self._L.lbpf_batch_get_schedule(self._h, ctypes.byref(v)), "lbpf_batch_get_schedule")
+        return {c: n for n, c in SCHEDULES.items()}[v.value]
+
     def close(self):
         if getattr(self, "_h", None):
             for s in self.sims:
@@ -286,6 +325,13 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def wait_probe(flag_value, polls):
+    """The step's bounded wait on its own (``lbpf_wait_probe``): True if it saw the flag."""
+    seen = ctypes.c_int32()
+    _check(load().lbpf_wait_probe(int(flag_value), int(polls), ctypes.byref(seen)), "lbpf_wait_probe")
+    return bool(seen.value)
 
 
 def batch_from_workloads(ws, storage=None, stream=None):

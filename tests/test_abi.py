@@ -36,10 +36,11 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_strerror(lib):
-    for code in (0, -1, -2, -3, -4, -6):
+    for code in (0, -1, -2, -3, -4, -5, -6):
         assert lib.lbpf_strerror(code) != b"unknown error"
     assert b"unstable" in lib.lbpf_strerror(-2)
-    assert lib.lbpf_strerror(-5) == b"unknown error"  # no call has a bounded device wait
+    assert b"bounded wait" in lib.lbpf_strerror(-5)  # the one-launch step's waits
+    assert lib.lbpf_strerror(-7) == b"unknown error"
 
 
 def test_signatures_follow_the_boundary(lib):
@@ -54,7 +55,8 @@ def test_signatures_follow_the_boundary(lib):
             "const lbpf_params* params, void* cuda_stream, lbpf_batch** out);") in flat
     assert "int lbpf_batch_from_sims(int32_t n, lbpf_sim* const* sims, void* cuda_stream, lbpf_batch** out);" in flat
     assert "int lbpf_batch_member(const lbpf_batch* batch, int32_t i, lbpf_sim** out);" in flat
-    assert "LBPF_ETIMEOUT" not in flat
+    assert "#define LBPF_ETIMEOUT (-5)" in src
+    assert "int lbpf_set_schedule(lbpf_sim* sim, int32_t schedule);" in flat
 
 
 def test_batch_and_tip_reject_bad_arguments_without_gpu(lib):
@@ -71,6 +73,14 @@ def test_batch_and_tip_reject_bad_arguments_without_gpu(lib):
     assert lib.lbpf_tip(None, 0, c, ctypes.byref(x), None) == lbpf.LBPF_EINVAL
     m = ctypes.c_void_p()
     assert lib.lbpf_batch_member(None, 0, ctypes.byref(m)) == lbpf.LBPF_EINVAL
+    ms = ctypes.c_double()
+    assert lib.lbpf_batch_autotune(None, 6, ctypes.byref(ms)) == lbpf.LBPF_EINVAL
+    assert lib.lbpf_batch_get_tiling(None, None, None) == lbpf.LBPF_EINVAL
+    assert lib.lbpf_set_schedule(None, 1) == lbpf.LBPF_EINVAL
+    assert lib.lbpf_batch_set_schedule(None, 0) == lbpf.LBPF_EINVAL
+    v = ctypes.c_int32()
+    assert lib.lbpf_get_schedule(None, ctypes.byref(v)) == lbpf.LBPF_EINVAL
+    assert lib.lbpf_wait_probe(1, 0, ctypes.byref(v)) == lbpf.LBPF_EINVAL  # no GPU work for bad arguments
 
 
 def _create(lattices=(19, 19, 0), grid=(8, 8, 8), **kw):

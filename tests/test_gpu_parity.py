@@ -378,6 +378,30 @@ def test_autotune_keeps_state():
         assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_batch_autotune_keeps_state(storage):
+    """lbpf_batch_autotune times every candidate tiling and restores each member: after it,
+    from an unaligned step count (7, not a multiple of the 6-step graph period), the batch
+    continues bit for bit like members that were never tuned, and the tiling it kept is
+    one of the candidates."""
+    ws = workloads.batch_sweep(count=3, storage=storage)
+    singles = [lbpf.sim_from_workload(w) for w in ws]
+    batch = lbpf.batch_from_workloads(ws)
+    batch.step(7)
+    ms = batch.autotune(steps=6)
+    assert ms > 0
+    by, zc = batch.get_tiling()
+    assert by in (4, 6, 8) and zc in (0, 12, 16, 24)
+    assert all(m.steps_done == 7 for m in batch.sims)
+    batch.step(11)
+    for s in singles:
+        s.step(18)
+    for s, m in zip(singles, batch.sims):
+        for x, y in zip(s.read_fields(), m.read_fields()):
+            assert np.array_equal(x, y)
+    batch.close()
+
+
 def test_nan_is_reported():
     shape, lat = (12, 12, 12), (19, 19, 0)
     params = workloads.base_params()
