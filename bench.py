@@ -377,6 +377,26 @@ def _timed(s, k):
     return ms_phi / k, ms_uth / k, span / k
 
 
+def fp64_peak_gflops(st, n=8192, reps=5):
+    """Measured FP64 arithmetic rate of this GPU: a cuBLAS DGEMM (2 n^3 flops), timed with
+    CUDA events on the bench stream after one warm-up; the denominator of the FP64 form."""
+    import torch
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(st):
+        c = a @ b
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            c = a @ b
+        e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    del a, b, c
+    torch.cuda.empty_cache()
+    return 2.0 * n ** 3 / (ms * 1e-3) / 1e9
+
+
 def run_variants(args, st):
     """The FP16-storage form at 512^3, the plain FP64 form at 256^3, the same 512^3 workload
     with interface at most sites, the 2D scheme in FP32 on 8192^2, and the batched FP16
@@ -400,6 +420,10 @@ def run_variants(args, st):
                      "phi_ms": phi_ms, "uth_ms": uth_ms, "alg_GBps": alg, "hbm_frac": alg / hbm}
         if name == "f64":
             out[name]["fp64_GFLOPs"] = glups * 687  # FP64 operations per site-update counted by ncu (halo included)
+            peak = fp64_peak_gflops(st)
+            out[name]["fp64_peak_GFLOPs"] = peak
+            out[name]["fp64_frac"] = glups * 687 / peak
+            out[name]["fp64_peak_source"] = "cuBLAS DGEMM 8192^3 through torch.matmul, CUDA events, this run"
         if name.startswith("dense"):
             out[name]["seeds"] = len(w.radii)
         s.close()
