@@ -107,6 +107,24 @@ def test_rejects_invalid_arguments(lib):
     assert _create(lattices=(5, 9, 0), grid=(8, 8, 1), storage=7) == lbpf.LBPF_EINVAL
 
 
+def test_grid_size_limit(lib):
+    """The step kernels address populations with 32-bit element offsets, so 19 x n_sites
+    must stay below 2^32: 608 x 608 x 612 sites (19 x 226,234,368 > 2^32) is refused before
+    any device work, for every lattice (the limit counts the largest lattice); the largest
+    grid that fits, 608 x 608 x 611, passes validation (without a GPU the call then fails
+    on the device, not on the size)."""
+    assert 19 * 608 * 608 * 612 >= 2 ** 32 > 19 * 608 * 608 * 611
+    for lat in ((19, 19, 0), (7, 7, 0), (15, 19, 7)):
+        assert _create(lattices=lat, grid=(608, 608, 612), dt=0.05) == lbpf.LBPF_EINVAL
+    if not _gpu_present():  # (with a GPU this would allocate the whole grid; the GPU test does that)
+        assert _create(grid=(608, 608, 611), dt=0.05) == lbpf.LBPF_ECUDA
+
+
+def _gpu_present():
+    import torch
+    return torch.cuda.is_available()
+
+
 def test_rejects_unstable_nonlocal_collision(lib):
     """eps = 0.05, dx = 0.8, dt = 0.01: a_s^2 eta_phi falls below 1/2 along <111>."""
     assert _create(eps1=0.05, dt=0.01) == lbpf.LBPF_EUNSTABLE

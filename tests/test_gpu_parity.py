@@ -468,6 +468,39 @@ def test_full_size_sampled_parity_kh512_f32():
     assert abs((b[2] - 0.5 * b[0]) - (a[2] - 0.5 * a[0])) < 1e-6 * w.sites
 
 
+def test_largest_grid_sampled_parity_f32():
+    """The largest grid the kernels' 32-bit element offsets allow: 608 x 608 x 611 sites, so
+    that 19 x n_sites is just below 2^32 (the next plane is refused, tests/test_abi.py).  FP32
+    with the benchmark's lattices, recipe and 8-row launch configuration (about 116 GB on the
+    device): one step from four seeds, sampled sites against oracle sub-box runs, among them
+    the far corner, whose last D3Q19 population sits 2^32 - 3.5 M elements into its array."""
+    grid = (608, 608, 611)
+    assert 19 * grid[0] * grid[1] * grid[2] < 2 ** 32 <= 19 * grid[0] * grid[1] * (grid[2] + 1)
+    w = workloads.large_kh(608)
+    gpu = lbpf.Sim(grid, w.lattices, storage="f32", **w.params)
+    gpu.init_seed(w.centres, w.radii, w.U0, w.theta0)
+    assert gpu.get_tiling()[0] == 8
+    gpu.step(1)
+    phi, U, th = gpu.read_fields()
+    gpu.close()
+    hi_all = np.array(grid)
+    pts = [np.minimum(p, hi_all - 1) for p in _sample_sites(608, w.centres, 16, seed=5)]
+    pts += [np.array([607, 607, 610]), np.array([0, 607, 610]), np.array([607, 0, 305]), np.array([301, 402, 609])]
+    for p in pts:
+        lo = np.maximum(p - 5, 0)
+        hi = np.minimum(p + 6, hi_all)
+        shape = tuple(int(v) for v in (hi - lo))
+        ora = oracle.Sim(shape, w.lattices, params=oracle_params(w.params))
+        ora.init_seed(w.centres - lo[None, :], w.radii, w.U0, w.theta0)
+        ora.step(1)
+        po, uo, to = ora.fields()
+        q = tuple(int(v) for v in (p - lo))
+        x, y, z = int(p[0]), int(p[1]), int(p[2])
+        assert abs(phi[z, y, x] - po[q[2], q[1], q[0]]) < 2e-6, tuple(p)
+        assert abs(U[z, y, x] - uo[q[2], q[1], q[0]]) < 2e-6, tuple(p)
+        assert abs(th[z, y, x] - to[q[2], q[1], q[0]]) < 2e-6, tuple(p)
+
+
 def test_grid_anisotropy_sphere_matches_oracle():
     """The isotropic-sphere set-up of Sec. 4.1 (pure substance, theta on D3Q7) on 51^3 for
     400 steps, phi on D3Q7 and D3Q19: the GPU FP64 fields track the oracle's and give the
