@@ -198,6 +198,13 @@ int lbpf_autotune(lbpf_sim* sim, int32_t steps, double* best_ms);
 #define LBPF_SCHED_ONE_LAUNCH 1
 int lbpf_set_schedule(lbpf_sim* sim, int32_t schedule);
 int lbpf_get_schedule(const lbpf_sim* sim, int32_t* schedule);
+/* Bound of each wait of the one-launch step, in polling rounds of about 0.25 us (default
+ * 2^22, about a second; the ordered schedule never needs more than the time one tile takes).
+ * 0 makes every wait give up at once: the step then runs with the flag of a failed wait set,
+ * and the next call that returns data reports LBPF_ETIMEOUT (sticky), which is how the
+ * failure path is tested without a device hang.  LBPF_EINVAL for a negative value.
+ * Synchronises the handle's stream; takes effect at the next step. */
+int lbpf_set_wait_polls(lbpf_sim* sim, int32_t polls);
 
 /* Diagnostic of the bounded wait the one-launch step uses: one warp waits on a device flag
  * initialised to `flag_value` for at most `polls` rounds (each about 0.25 us); *seen is 1

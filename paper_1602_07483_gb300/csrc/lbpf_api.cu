@@ -22,6 +22,7 @@ using namespace lbpf;
 namespace {
 
 constexpr int kGraphSteps = 6;
+constexpr unsigned kWaitPolls = 1u << 22;  // default bound of a one-launch wait: about a second
 #ifndef LBPF_ONE_LAUNCH_LAG_PCT
 #define LBPF_ONE_LAUNCH_LAG_PCT 100  // lag of the one-launch schedule, % of the resident blocks
 #endif
@@ -93,6 +94,7 @@ struct OneLaunch {
   StepSched sc{};
   int grid = 0;               // resident blocks on the device
   size_t smem = 0;
+  unsigned polls = kWaitPolls;  // bound of each wait (lbpf_set_wait_polls)
 };
 
 struct lbpf_sim {
@@ -271,6 +273,7 @@ int setup_one_launch(OneLaunch& ol, const std::vector<WorkItem>& items, const st
   ol.sc.ctl = ol.d_ctl;
   ol.sc.err = d_err;
   ol.sc.ntickets = (int)order.size();
+  ol.sc.polls = ol.polls;
   ol.grid = std::min(resident, ol.sc.ntickets);
   ol.smem = smem;
   return LBPF_OK;
@@ -883,6 +886,19 @@ int lbpf_set_schedule(lbpf_sim* s, int32_t schedule) {
   }
   if (!s->ol.on) free_one_launch(s->ol);
   return rc;
+}
+
+int lbpf_set_wait_polls(lbpf_sim* s, int32_t polls) {
+  if (!s || polls < 0) return LBPF_EINVAL;
+  if (status(s)) return s->sticky;
+  CK(s, cudaStreamSynchronize(s->stream));
+  s->ol.polls = (unsigned)polls;
+  if (s->ol.d_sched) s->ol.sc.polls = s->ol.polls;
+  // the step graph holds the launch parameters: capture it again at the next step
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  s->gexec = nullptr;
+  s->graph_ok = false;
+  return LBPF_OK;
 }
 
 int lbpf_get_schedule(const lbpf_sim* s, int32_t* schedule) {

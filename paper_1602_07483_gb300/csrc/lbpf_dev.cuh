@@ -1200,11 +1200,9 @@ struct StepSched {
   unsigned* ctl;       // ctl[0]: next ticket; ctl[1 + j]: phase-field tile of item j done (zeroed before each launch)
   int* err;            // set to 1 when a wait gave up
   int ntickets;
+  unsigned polls;      // bound of each wait (rounds of about 0.25 us)
 };
 
-#ifndef LBPF_WAIT_POLLS
-#define LBPF_WAIT_POLLS (1u << 22)  // polls of about 0.25 us each: about a second
-#endif
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
   unsigned v;
@@ -1249,7 +1247,7 @@ __global__ void __launch_bounds__(32 * MAX_BLOCK_ROWS, sizeof(S) == 8 ? LBPF_UTH
       const int j = ~w;
       if (threadIdx.y == 0) {
         const int b = __ldg(sc.dep_off + j), n = __ldg(sc.dep_off + j + 1) - b;
-        if (!wait_done(sc.ctl + 1, sc.dep + b, n, LBPF_WAIT_POLLS) && threadIdx.x == 0) atomicExch(sc.err, 1);
+        if (!wait_done(sc.ctl + 1, sc.dep + b, n, sc.polls) && threadIdx.x == 0) atomicExch(sc.err, 1);
       }
       __syncthreads();
       uth_tile<QU, QT, S, true, 0>(sims, items[j], s6);

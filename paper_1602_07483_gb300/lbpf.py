@@ -86,6 +86,7 @@ def load(path: str = LIB_PATH):
             "lbpf_get_tiling": ([_VP, ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
             "lbpf_autotune": ([_VP, i32, _D], ctypes.c_int),
             "lbpf_set_schedule": ([_VP, i32], ctypes.c_int),
+            "lbpf_set_wait_polls": ([_VP, i32], ctypes.c_int),
             "lbpf_get_schedule": ([_VP, ctypes.POINTER(i32)], ctypes.c_int),
             "lbpf_wait_probe": ([i32, i32, ctypes.POINTER(i32)], ctypes.c_int),
             "lbpf_destroy": ([_VP], ctypes.c_int),
@@ -239,6 +240,10 @@ class Sim:
     def set_schedule(self, schedule):
         """``"two_kernels"`` or ``"one_launch"`` (``lbpf_set_schedule``)."""
         _check(self._L.lbpf_set_schedule(self._h, SCHEDULES[schedule]), "lbpf_set_schedule")
+
+    def set_wait_polls(self, polls):
+        """Bound of each one-launch wait (``lbpf_set_wait_polls``)."""
+        _check(self._L.lbpf_set_wait_polls(self._h, int(polls)), "lbpf_set_wait_polls")
 
     @property
     def schedule(self):

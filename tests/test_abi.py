@@ -77,6 +77,7 @@ def test_batch_and_tip_reject_bad_arguments_without_gpu(lib):
     assert lib.lbpf_batch_autotune(None, 6, ctypes.byref(ms)) == lbpf.LBPF_EINVAL
     assert lib.lbpf_batch_get_tiling(None, None, None) == lbpf.LBPF_EINVAL
     assert lib.lbpf_set_schedule(None, 1) == lbpf.LBPF_EINVAL
+    assert lib.lbpf_set_wait_polls(None, 10) == lbpf.LBPF_EINVAL
     assert lib.lbpf_batch_set_schedule(None, 0) == lbpf.LBPF_EINVAL
     v = ctypes.c_int32()
     assert lib.lbpf_get_schedule(None, ctypes.byref(v)) == lbpf.LBPF_EINVAL

@@ -6,7 +6,8 @@ tickets and done flags, so every field must agree bit for bit with the two-kerne
 triple, under tilings whose U/theta rings reach one or two z-chunks away, in single steps
 and in graph replays, for single handles and for batches.  The bounded wait that the
 launch's blocks use is exercised on its own: it returns when the flag is set, gives up on
-a flag that nothing sets, and the device stays usable after it gave up.
+a flag that nothing sets, and the device stays usable after it gave up; and a step whose
+waits are bounded to nothing reports LBPF_ETIMEOUT on its handle.
 """
 import time
 
@@ -134,3 +135,26 @@ def test_bounded_wait_gives_up_and_device_stays_usable():
     s.set_schedule("one_launch")
     s.step(6)
     assert np.all(np.isfinite(s.sums()))
+
+
+def test_wait_that_gives_up_is_reported():
+    """The failure path of the one-launch step without a hang: with each wait bounded to zero
+    polls every U/theta tile gives up at once (nothing spins), sets the handle's flag and
+    goes ahead; the next call that returns data reports LBPF_ETIMEOUT, the handle stays
+    failed, and the device stays usable for another handle."""
+    w = workloads.coupled_dendrite(n=32)
+    s = lbpf.sim_from_workload(w, storage="f32")
+    s.set_schedule("one_launch")
+    s.set_wait_polls(0)
+    s.step(6)
+    with pytest.raises(lbpf.LbpfError) as e:
+        s.sums()
+    assert e.value.code == lbpf.LBPF_ETIMEOUT
+    with pytest.raises(lbpf.LbpfError) as e:
+        s.step(1)
+    assert e.value.code == lbpf.LBPF_ETIMEOUT
+    t = lbpf.sim_from_workload(w, storage="f32")
+    t.set_schedule("one_launch")
+    t.step(6)
+    assert np.all(np.isfinite(t.sums()))
+
