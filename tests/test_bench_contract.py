@@ -46,6 +46,7 @@ def test_own_arm_line_small():
     e = d["e2e"]
     assert e["value"] > 0 and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
     assert d["gpu_launches"] == 2 * d["steps"]
+    assert sum(d["runs"]["steps"]) == d["steps"] and d["runs"]["median_GLUPS"] > 0
     assert d["config"]["workload"].startswith("kh64")
     dev = d["developed"]
     assert dev["GLUPS"] > 0 and dev["after_steps"] >= 2000
